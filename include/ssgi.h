@@ -1,0 +1,209 @@
+/*
+ * ssgi.h -- C ABI of the GB300 (sm_103a) screen-space global-illumination library.
+ *
+ * Method: "3D Gaussian Inverse Rendering with Approximated Global Illumination"
+ * (arXiv 2504.01358).  The library implements the paper's data-parallel hot path on a
+ * rasterised G-buffer:
+ *   - direct split-sum shading from an environment map (Sec. 3.2 "Shading"),
+ *   - Monte-Carlo screen-space ray tracing for one-bounce indirect light against a
+ *     hierarchical-Z pyramid (Sec. 3.3, Appendix D),
+ *   - the adjoint of both with the march frozen (backward pass for inverse rendering),
+ *   - a continuous-batching serving loop (ssgi_serve_*).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Memory.  Every array pointer is a DEVICE pointer owned by the caller unless the argument
+ *   says "host".  The library never frees or retains caller memory; it allocates nothing
+ *   except inside ssgi_serve_create.  All arrays are dense, C-contiguous FP32 (int32 for
+ *   hit indices), 4-byte aligned.
+ * Streams.  Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL = the legacy
+ *   default stream).  A call returns after argument validation and launch; device-side
+ *   faults surface as SSGI_ERR_CUDA from this or a later call.
+ * Errors.  Every call returns an ssgi_status.  On any non-OK status nothing was enqueued
+ *   unless the status is SSGI_ERR_CUDA from a launch, in which case earlier launches of the
+ *   same call may have run.  ssgi_status_string() names a status.
+ * Layouts.  G-buffer planes are [V,H,W] (depth, roughness, metallic) or [V,H,W,3] (normal,
+ *   albedo); images c_d, c_s, c1, final are [V,H,W,3]; hit indices [V,H,W,spp].
+ * Camera.  World is right-handed with y up.  cam_to_world is 3x4 row-major [R | eye]; the
+ *   columns of R are the camera's right, up and back axes in world space (the camera looks
+ *   down its -z).  Pinhole, vertical FOV, pixel (x, y) centre at (x + 0.5, y + 0.5), y down,
+ *   focal length f = (H/2) / tan(fov_y/2), principal point (W/2, H/2).
+ * Depth.  Linear depth (distance along the camera's forward axis).  A pixel whose depth is
+ *   not finite and positive is background: it shows the environment in its view direction
+ *   and casts no rays.
+ * Environment.  Lat-long RGB map, h x w with h, w powers of two and w >= h; direction d maps
+ *   to u = 0.5 + atan2(d.x, -d.z) / (2 pi), v = atan2(sqrt(d.x^2 + d.z^2), d.y) / pi (v = 0 is
+ *   +y); texel (i, j) centre at ((j + 0.5)/w, (i + 0.5)/h); bilinear, u wraps, v clamps.
+ *   The mip chain has levels = log2(h) + 1; level l is the 2x2 box mean of level l-1; all
+ *   levels packed level 0 first, each [h>>l][w>>l][3].  lambda_max = levels - 1.
+ * RNG.  Sample s of pixel p (row-major index within its view) of view v draws Philox4x32-10
+ *   (Salmon et al., SC'11) with counter (p, s, 0, 0) and key (seed_lo, seed_hi ^ v);
+ *   xi_k = (out_k >> 8) * 2^-24.
+ */
+#ifndef SSGI_H
+#define SSGI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void *ssgi_stream_t; /* cudaStream_t */
+
+typedef enum {
+  SSGI_OK = 0,
+  SSGI_ERR_INVALID_ARG = 1, /* null pointer, bad size, unsupported combination of sizes */
+  SSGI_ERR_UNSUPPORTED = 2, /* valid request this build cannot serve (e.g. too many views) */
+  SSGI_ERR_CUDA = 3,        /* a CUDA call or launch failed */
+  SSGI_ERR_OOM = 4,         /* an allocation inside ssgi_serve_create failed */
+  SSGI_ERR_BUDGET = 5,      /* serving: request larger than the device-memory budget */
+  SSGI_ERR_QUEUE_FULL = 6,  /* serving: no free queue entry */
+  SSGI_ERR_TIMEOUT = 7,     /* a bounded wait ran out (host or device side) */
+  SSGI_ERR_NOT_READY = 8,   /* serving: result not finished yet */
+  SSGI_ERR_CANCELLED = 9    /* serving: request was cancelled or the server shut down */
+} ssgi_status;
+
+#define SSGI_MAX_VIEWS 32
+#define SSGI_MAX_HIZ_LEVELS 16
+#define SSGI_MAX_ENV_LEVELS 16
+
+/* hit_idx codes: >= 0 is the hit pixel's row-major index within the view */
+#define SSGI_HIT_MISS (-1)       /* left the screen, passed the near plane or ray length, or ran out of steps */
+#define SSGI_HIT_INVALID (-2)    /* sample below the surface (n.v <= 0 or n.w <= 0): weight 0 */
+#define SSGI_HIT_BACKGROUND (-3) /* background pixel: no rays */
+
+/* ssgi_trace_params.flags */
+#define SSGI_DIFFUSE_INDIRECT 1u /* also estimate diffuse indirect light from the same rays and add it to final */
+#define SSGI_BRUTE_FORCE 2u      /* ignore the pyramid: walk every pixel, no step budget (reference mode) */
+
+typedef struct { int32_t views, height, width; } ssgi_dims;
+
+/* One camera per view (host memory).  Same 14 floats as the input generator's record. */
+typedef struct {
+  float cam_to_world[12];
+  float fov_y_rad;
+  float z_near;
+} ssgi_camera;
+
+/* Device planes of a G-buffer (Sec. 3.2, eq:g-buffer): depth [V,H,W], normal [V,H,W,3]
+ * (unit, world space), albedo [V,H,W,3] in [0,1], roughness [V,H,W] in [0,1] (GGX alpha,
+ * eq:ndf), metallic [V,H,W] in [0,1]. */
+typedef struct {
+  const float *depth, *normal, *albedo, *rough, *metal;
+  ssgi_dims d;
+} ssgi_gbuffer;
+
+/* Device environment mip chain (Sec. 3.2, SampleEnvMap), as built by ssgi_build_env_mips. */
+typedef struct {
+  const float *mips;
+  int32_t h, w, levels;
+} ssgi_envmap;
+
+/* Trace parameters (Sec. 3.3; Appendix D's threshold and maxRayLength). */
+typedef struct {
+  int32_t spp;        /* rays per pixel, N_s (paper: 8) -- 1..1024 */
+  int32_t max_steps;  /* march iterations (skip, refine or test) before a ray counts as a miss, >= 0 */
+  int32_t hiz_levels; /* pyramid levels including level 0 = depth, 1..SSGI_MAX_HIZ_LEVELS */
+  float thickness;    /* a hit needs the ray to pass behind the depth buffer by at most this (world units) */
+  float max_distance; /* ray length in world units (> 0) */
+  uint64_t seed;      /* RNG key */
+  uint32_t flags;     /* SSGI_DIFFUSE_INDIRECT | SSGI_BRUTE_FORCE */
+} ssgi_trace_params;
+
+/* ---------------------------------------------------------------------------------------- */
+/* Sizes (pure host functions; 0 / -1 on invalid input)                                      */
+/* ---------------------------------------------------------------------------------------- */
+const char *ssgi_status_string(ssgi_status s);
+const char *ssgi_version(void);
+/* number of mip levels of an h x w map, or -1 if h, w are not powers of two with w >= h */
+int32_t ssgi_env_levels(int32_t h, int32_t w);
+/* floats in the packed mip chain of an h x w RGB map */
+size_t ssgi_env_mip_floats(int32_t h, int32_t w);
+/* floats in the packed pyramid of all views: per view, levels 1..levels-1 of ceil(H/2^l) x
+ * ceil(W/2^l) cells, level after level; views one after another */
+size_t ssgi_hiz_floats(ssgi_dims d, int32_t levels);
+/* bytes of scratch ssgi_backward needs */
+size_t ssgi_backward_workspace_bytes(ssgi_dims d, int32_t env_h, int32_t env_w);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Precomputation                                                                           */
+/* ---------------------------------------------------------------------------------------- */
+/* BRDF-integral table of the split sum (Sec. 3.2 "Shading", Appendix C): lut[(i*n + j)*2 + k]
+ * for roughness (i + 0.5)/n and n.v = (j + 0.5)/n; k = 0 is A (F0 scale), k = 1 is B (bias),
+ * so that int f_s cos = F0 A + B.  Monte-Carlo over `samples` GGX half vectors at Hammersley
+ * points (xi0 = (k + 0.5)/samples, xi1 = radical inverse of k).  n in [2, 1024], samples in
+ * [1, 1<<20].  Output: 2 n^2 floats. */
+ssgi_status ssgi_build_brdf_lut(int32_t n, int32_t samples, float *lut_out, ssgi_stream_t stream);
+
+/* Environment mip chain (Sec. 3.2, SampleEnvMap): env [h][w][3] -> mips_out
+ * (ssgi_env_mip_floats(h, w) floats; level 0 is a copy of env). */
+ssgi_status ssgi_build_env_mips(const float *env, int32_t h, int32_t w, float *mips_out, ssgi_stream_t stream);
+
+/* Hierarchical-Z pyramid (McGuire & Mara 2014, cited in Sec. 3.3): level l cell (i, j) is
+ * the minimum depth over the level-0 pixels [i 2^l, (i+1) 2^l) x [j 2^l, (j+1) 2^l) inside
+ * the image.  depth [V,H,W] -> hiz_out (ssgi_hiz_floats(d, levels) floats).  levels in
+ * [1, SSGI_MAX_HIZ_LEVELS]; levels == 1 writes nothing. */
+ssgi_status ssgi_build_hiz(const float *depth, ssgi_dims d, int32_t levels, float *hiz_out, ssgi_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Forward                                                                                  */
+/* ---------------------------------------------------------------------------------------- */
+/* Direct shading (Sec. 3.2 "Shading"): per pixel v = unit vector to the camera,
+ * r = 2 (v.n) n - v, lambda = log2(rho + 1) lambda_max, (A, B) = bilinear table lookup at
+ * (rho, clamp(n.v, 1e-4, 1)), F0 = lerp(0.04, albedo, metallic) (Appendix B);
+ *   c_s = L_E(r, lambda) (F0 A + B),  c_d = (1 - m) a L_E(n, lambda),  c1 = c_d + c_s.
+ * Background pixels: c_d = c_s = 0, c1 = L_E(view direction, 0).
+ * cams: host array of d.views cameras.  lut: 2 lut_n^2 floats from ssgi_build_brdf_lut.
+ * Outputs [V,H,W,3]; c_s may be NULL. */
+ssgi_status ssgi_shade_direct(const ssgi_gbuffer *g, const ssgi_camera *cams, const ssgi_envmap *env,
+                              const float *lut, int32_t lut_n, float *c_d, float *c_s, float *c1,
+                              ssgi_stream_t stream);
+
+/* Monte-Carlo screen-space ray tracing (Sec. 3.3, Appendix D) and composite.  Per pixel and
+ * sample: GGX half vector h (alpha = rho) around n, w = 2 (v.h) h - v; the screen-space
+ * march finds the first pixel q != origin where the ray's depth interval over q reaches
+ * behind depth(q) by at most `thickness` (hierarchical-Z skipping never changes that pixel);
+ * L = c1[q] on a hit, else L_E(w, 0).  c_s' = 1/spp sum F G (v.h) / ((n.v)(n.h)) L (invalid
+ * samples count as 0); final = c_d + c_s' (+ c_id with SSGI_DIFFUSE_INDIRECT, where
+ * c_id = (1 - m) a / pi * 1/spp sum L (n.w) / p, p = D (n.h) / (4 v.h)).
+ * hiz: ssgi_build_hiz output for p->hiz_levels (may be NULL when hiz_levels == 1 or with
+ * SSGI_BRUTE_FORCE).  c1, c_d: ssgi_shade_direct outputs.  Outputs: final [V,H,W,3];
+ * c_s_mc, c_id [V,H,W,3] and hit_idx [V,H,W,spp] are optional (NULL).  step_count (one
+ * device uint64, optional) has the total number of march iterations of the call added to
+ * it atomically (the caller zeroes it); this is the traversal work of the launch. */
+ssgi_status ssgi_trace_indirect(const ssgi_gbuffer *g, const ssgi_camera *cams, const float *hiz, const float *c1,
+                                const float *c_d, const ssgi_envmap *env, const ssgi_trace_params *p,
+                                float *c_s_mc, float *c_id, float *final_out, int32_t *hit_idx,
+                                uint64_t *step_count, ssgi_stream_t stream);
+
+/* L2 loss against a target: loss = mean((final - target)^2) over n floats, and
+ * g_final = 2 (final - target) / n.  loss_out (one device float) may be NULL. */
+ssgi_status ssgi_l2_loss(const float *final_in, const float *target, int64_t n, float *g_final, float *loss_out,
+                         ssgi_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Backward (adjoint).  The paper's march is not differentiable (Sec. 5); the hits, the      */
+/* sampled directions and the sampling pdf are frozen at their forward values ("replay"),  */
+/* and the adjoint is exact for that replay function:                                       */
+/*   per sample  f_s(w; theta) (n.w) / p_frozen * L(theta),  f_s = D F G / (4 (n.w)(n.v)).   */
+/* ---------------------------------------------------------------------------------------- */
+/* Inputs: g_final = d loss / d final [V,H,W,3]; the forward's G-buffer, cameras, c1, env,
+ * table, stored hit_idx [V,H,W,spp] and the same params.  Outputs (overwritten):
+ * g_albedo [V,H,W,3], g_rough [V,H,W], g_metal [V,H,W], g_normal [V,H,W,3] and
+ * g_env [h][w][3] (base level of the environment; the mip-chain adjoint is included).
+ * workspace: >= ssgi_backward_workspace_bytes(d, env->h, env->w) bytes of device scratch,
+ * 16-byte aligned, cleared by the call.  Pixels whose normal points exactly at a pole of
+ * the lat-long map (+-y) get no gradient through the direction of that lookup (the map is
+ * not differentiable there). */
+ssgi_status ssgi_backward(const float *g_final, const ssgi_gbuffer *g, const ssgi_camera *cams, const float *c1,
+                          const ssgi_envmap *env, const float *lut, int32_t lut_n, const int32_t *hit_idx,
+                          const ssgi_trace_params *p, float *g_albedo, float *g_rough, float *g_metal,
+                          float *g_normal, float *g_env, void *workspace, size_t ws_bytes, ssgi_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSGI_H */

@@ -1,0 +1,246 @@
+// k_trace.cu -- Monte-Carlo screen-space ray tracing for one-bounce indirect light
+// (Sec. 3.3, Appendix D) with a conservative hierarchical-Z traversal, plus the Monte-Carlo
+// sum and the composite final = c_d + c_s'.
+//
+// March definition: the ray o + t w is clipped to z >= z_near and t <= max_distance and
+// projected to the screen segment P(s) = P0 + s D, s in [0, 1], along which 1/z is linear in
+// s.  The state is a level-0 pixel (ix, iy) entered at parameter s and a level L.  Each
+// iteration takes the level-L cell holding (ix, iy) and the ray's depth interval over
+// [s, min(s_exit, 1)]:
+//   entirely in front of the cell's minimum depth            -> skip the cell, go up a level;
+//   otherwise, above level 0                                 -> go down a level;
+//   at level 0, reaching no deeper than depth + thickness    -> hit (ix, iy);
+//   at level 0 otherwise (passes behind)                     -> step to the next pixel.
+// Leaving a cell through its x side (ties go to x) enters the pixel across that side, on
+// the row of the exit point clamped to the cell's rows; symmetrically for y.  The origin
+// pixel is left before the first iteration and is never a hit.  Off screen, past the end of
+// the segment, or max_steps iterations without a hit is a miss.  The skip test is
+// conservative, so the first hit is the one a pixel-by-pixel walk finds.
+#include <limits.h>
+
+#include "ssgi_device.cuh"
+
+namespace ssgi {
+
+struct TraceArgs {
+  Views vs;
+  EnvInfo e;
+  HizInfo hz;
+  const float* __restrict__ depth;
+  const float* __restrict__ normal;
+  const float* __restrict__ albedo;
+  const float* __restrict__ rough;
+  const float* __restrict__ metal;
+  const float* __restrict__ hiz;
+  const float* __restrict__ c1;
+  const float* __restrict__ c_d;
+  const float* __restrict__ mips;
+  float* __restrict__ c_s_mc;
+  float* __restrict__ c_id;
+  float* __restrict__ final_out;
+  int32_t* __restrict__ hit_idx;
+  unsigned long long* step_count;
+  int spp, max_steps, levels;
+  float thickness, max_distance;
+  uint64_t seed;
+  uint32_t flags;
+};
+
+constexpr int kTileW = 8;   // a warp covers an 8 x 4 pixel tile
+constexpr int kTileH = 16;  // a 128-thread block covers 8 x 16 pixels
+
+struct Seg {
+  float P0x, P0y, Dx, Dy, iDx, iDy;
+};
+
+// Exit parameters of the level-L cell holding pixel (ix, iy) through its x and y sides.
+__device__ __forceinline__ void cell_exit(const Seg& g, int ix, int iy, int L, float& sx, float& sy) {
+  const int S = 1 << L;
+  const int cxl = ix >> L, cyl = iy >> L;
+  sx = INFINITY;
+  sy = INFINITY;
+  if (g.Dx != 0.0f) sx = ((float)(g.Dx > 0.0f ? (cxl + 1) * S : cxl * S) - g.P0x) * g.iDx;
+  if (g.Dy != 0.0f) sy = ((float)(g.Dy > 0.0f ? (cyl + 1) * S : cyl * S) - g.P0y) * g.iDy;
+}
+
+// Move (ix, iy) to the pixel entered when the ray leaves the level-L cell.
+__device__ __forceinline__ void cell_step(const Seg& g, int L, float sx, float sy, int& ix, int& iy, float& s) {
+  const int S = 1 << L;
+  const int cxl = ix >> L, cyl = iy >> L;
+  if (sx <= sy) {
+    const float fy = fminf(fmaxf(floorf(fmaf(sx, g.Dy, g.P0y)), (float)(cyl * S)), (float)(cyl * S + S - 1));
+    ix = g.Dx > 0.0f ? (cxl + 1) * S : cxl * S - 1;
+    iy = (int)fy;
+    s = sx;
+  } else {
+    const float fx = fminf(fmaxf(floorf(fmaf(sy, g.Dx, g.P0x)), (float)(cxl * S)), (float)(cxl * S + S - 1));
+    iy = g.Dy > 0.0f ? (cyl + 1) * S : cyl * S - 1;
+    ix = (int)fx;
+    s = sy;
+  }
+}
+
+// March from pixel (x, y) at linear depth z0 along camera-space direction w.  Returns the
+// hit pixel's index within the view, or SSGI_HIT_MISS.
+__device__ __forceinline__ int march(const TraceArgs& A, const DevCam& c, const float* __restrict__ dep,
+                                     const float* __restrict__ hz_v, int levels, int max_steps, int x, int y,
+                                     float z0, float3 w, int& it) {
+  const int H = A.vs.H, W = A.vs.W;
+  it = 0;
+  const float3 o = pix_dir_cam(c, x, y) * z0;
+  const float wz = -w.z;
+  float t_end = A.max_distance;
+  if (wz < 0.0f) t_end = fminf(t_end, (c.znear - z0) / wz);
+  if (!(t_end > 0.0f)) return SSGI_HIT_MISS;
+  const float3 X1 = o + w * t_end;
+  const float z1 = -X1.z;
+  Seg g;
+  g.P0x = (float)x + 0.5f;
+  g.P0y = (float)y + 0.5f;
+  g.Dx = (c.cx + c.f * X1.x / z1) - g.P0x;
+  g.Dy = (c.cy - c.f * X1.y / z1) - g.P0y;
+  g.iDx = 1.0f / g.Dx;
+  g.iDy = 1.0f / g.Dy;
+  const float k0 = 1.0f / z0, dk = 1.0f / z1 - k0;
+
+  int ix = x, iy = y;
+  float s = 0.0f, sx, sy;
+  cell_exit(g, ix, iy, 0, sx, sy);  // leave the origin pixel untested
+  if (!(fminf(sx, sy) < 1.0f)) return SSGI_HIT_MISS;
+  cell_step(g, 0, sx, sy, ix, iy, s);
+
+  int L = 0;
+  for (it = 0;; ++it) {
+    if (ix < 0 || ix >= W || iy < 0 || iy >= H) return SSGI_HIT_MISS;
+    if (it >= max_steps) return SSGI_HIT_MISS;
+    cell_exit(g, ix, iy, L, sx, sy);
+    const float se = fminf(sx, sy);
+    const float sb = fminf(se, 1.0f);
+    const float za = 1.0f / fmaf(s, dk, k0), zb = 1.0f / fmaf(sb, dk, k0);
+    const float zlo = fminf(za, zb), zhi = fmaxf(za, zb);
+    const float hzv = (L == 0) ? __ldg(dep + iy * W + ix)
+                               : __ldg(hz_v + A.hz.off[L] + (iy >> L) * A.hz.w[L] + (ix >> L));
+    if (zhi < hzv) {
+      if (!(se < 1.0f)) return SSGI_HIT_MISS;
+      cell_step(g, L, sx, sy, ix, iy, s);
+      if (L + 1 < levels) ++L;
+    } else if (L > 0) {
+      --L;
+    } else if (zlo <= hzv + A.thickness) {
+      return iy * W + ix;
+    } else {
+      if (!(se < 1.0f)) return SSGI_HIT_MISS;
+      cell_step(g, 0, sx, sy, ix, iy, s);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128) k_trace(TraceArgs A) {
+  const int W = A.vs.W, H = A.vs.H;
+  const int x = blockIdx.x * kTileW + (threadIdx.x % kTileW);
+  const int y = blockIdx.y * kTileH + (threadIdx.x / kTileW);
+  const int view = blockIdx.z;
+  if (x >= W || y >= H) return;
+  const long long HW = (long long)H * W;
+  const int rem = y * W + x;
+  const long long p = (long long)view * HW + rem;
+  const int spp = A.spp;
+  const float z0 = __ldg(A.depth + p);
+  if (is_background(z0)) {
+    const float3 v1 = ld3(A.c1 + 3 * p);
+    st3(A.final_out + 3 * p, v1);
+    if (A.c_s_mc) st3(A.c_s_mc + 3 * p, f3(0.f, 0.f, 0.f));
+    if (A.c_id) st3(A.c_id + 3 * p, f3(0.f, 0.f, 0.f));
+    if (A.hit_idx)
+      for (int s = 0; s < spp; ++s) A.hit_idx[p * spp + s] = SSGI_HIT_BACKGROUND;
+    return;
+  }
+  const DevCam& cam = A.vs.cam[view];
+  const bool brute = (A.flags & SSGI_BRUTE_FORCE) != 0;
+  const int levels = brute ? 1 : A.levels;
+  const int max_steps = brute ? INT_MAX : A.max_steps;
+  const float* dep = A.depth + view * HW;
+  const float* hz_v = A.hiz ? A.hiz + (long long)view * A.hz.per_view : nullptr;
+
+  const float3 d = pix_dir_world(cam, x, y);
+  const float3 v = d * (-1.0f / sqrtf(dot3(d, d)));
+  const float3 n = ld3(A.normal + 3 * p);
+  const float nv = dot3(n, v);
+  const float rho = __ldg(A.rough + p), m = __ldg(A.metal + p);
+  const float3 a = ld3(A.albedo + 3 * p);
+  const float3 F0 = f3(f0_of(a.x, m), f0_of(a.y, m), f0_of(a.z, m));
+  const float g1v = ggx_G1(nv, rho);
+  const bool want_cid = (A.flags & SSGI_DIFFUSE_INDIRECT) != 0;
+  float3 acc = f3(0.f, 0.f, 0.f), accd = f3(0.f, 0.f, 0.f);
+  unsigned long long steps = 0;
+
+  for (int s = 0; s < spp; ++s) {
+    const float2 xi = sample_uniforms(A.seed, view, (uint32_t)rem, (uint32_t)s);
+    const Sample sm = make_sample(n, v, nv, rho, xi);
+    int q = SSGI_HIT_INVALID;
+    if (sm.valid) {
+      int it;
+      q = march(A, cam, dep, hz_v, levels, max_steps, x, y, z0, world_to_cam(cam, sm.w), it);
+      steps += (unsigned long long)it;
+      const float3 Li = q >= 0 ? ld3(A.c1 + 3 * (view * HW + q)) : env_lookup0(A.mips, A.e, sm.w);
+      const float K = ggx_G1(sm.nw, rho) * g1v * sm.vh / (nv * sm.nh);
+      const float fc = pow5(1.0f - sm.vh);
+      const float3 F = F0 + (f3(1.f, 1.f, 1.f) - F0) * fc;
+      acc = acc + mul3(F, Li) * K;
+      if (want_cid) {
+        const float pdf = ggx_D(sm.nh, rho) * sm.nh / (4.0f * sm.vh);
+        if (pdf > 0.0f && isfinite(pdf)) accd = accd + mul3(a, Li) * ((1.0f - m) * kInvPi * sm.nw / pdf);
+      }
+    }
+    if (A.hit_idx) A.hit_idx[p * spp + s] = q;
+  }
+  const float3 csm = f3(acc.x / (float)spp, acc.y / (float)spp, acc.z / (float)spp);
+  const float3 cid = f3(accd.x / (float)spp, accd.y / (float)spp, accd.z / (float)spp);
+  float3 fin = ld3(A.c_d + 3 * p) + csm;
+  if (want_cid) fin = fin + cid;
+  st3(A.final_out + 3 * p, fin);
+  if (A.c_s_mc) st3(A.c_s_mc + 3 * p, csm);
+  if (A.c_id) st3(A.c_id + 3 * p, cid);
+  if (A.step_count && steps) atomicAdd(A.step_count, steps);
+}
+
+}  // namespace ssgi
+
+using namespace ssgi;
+
+extern "C" ssgi_status ssgi_trace_indirect(const ssgi_gbuffer* g, const ssgi_camera* cams, const float* hiz,
+                                           const float* c1, const float* c_d, const ssgi_envmap* env,
+                                           const ssgi_trace_params* p, float* c_s_mc, float* c_id, float* final_out,
+                                           int32_t* hit_idx, uint64_t* step_count, ssgi_stream_t stream) {
+  if (gbuffer_ok(g) != SSGI_OK || trace_params_ok(p) != SSGI_OK || !c1 || !c_d || !final_out)
+    return SSGI_ERR_INVALID_ARG;
+  const bool brute = (p->flags & SSGI_BRUTE_FORCE) != 0;
+  if (!brute && p->hiz_levels > 1 && !hiz) return SSGI_ERR_INVALID_ARG;
+  TraceArgs A;
+  if (make_views(cams, g->d, &A.vs) != SSGI_OK || make_env(env, &A.e) != SSGI_OK) return SSGI_ERR_INVALID_ARG;
+  make_hiz_info(g->d, p->hiz_levels, &A.hz);
+  A.depth = g->depth;
+  A.normal = g->normal;
+  A.albedo = g->albedo;
+  A.rough = g->rough;
+  A.metal = g->metal;
+  A.hiz = hiz;
+  A.c1 = c1;
+  A.c_d = c_d;
+  A.mips = env->mips;
+  A.c_s_mc = c_s_mc;
+  A.c_id = c_id;
+  A.final_out = final_out;
+  A.hit_idx = hit_idx;
+  A.step_count = reinterpret_cast<unsigned long long*>(step_count);
+  A.spp = p->spp;
+  A.max_steps = p->max_steps;
+  A.levels = p->hiz_levels;
+  A.thickness = p->thickness;
+  A.max_distance = p->max_distance;
+  A.seed = p->seed;
+  A.flags = p->flags;
+  dim3 grid(ceil_div(g->d.width, kTileW), ceil_div(g->d.height, kTileH), g->d.views);
+  k_trace<<<grid, kTileW * kTileH, 0, (cudaStream_t)stream>>>(A);
+  return launch_status();
+}

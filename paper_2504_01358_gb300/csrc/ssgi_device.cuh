@@ -1,0 +1,280 @@
+// ssgi_device.cuh -- device-side math shared by the SSGI kernels (FP32, sm_103a).
+//
+// Microfacet terms (Appendix B), the lat-long environment lookup with its mip blend
+// (Sec. 3.2, SampleEnvMap), the BRDF-table lookup (Appendix C), GGX sampling (Sec. 3.3) and
+// the Philox4x32-10 generator (Salmon et al., SC'11).  Everything here follows the data
+// formats of include/ssgi.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ssgi_internal.h"
+
+namespace ssgi {
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kInv2Pi = 0.15915494309189533577f;
+constexpr float kInvPi = 0.31830988618379067154f;
+
+// ------------------------------------------------------------------------------------------
+// float3 helpers
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 mul3(float3 a, float3 b) { return f3(a.x * b.x, a.y * b.y, a.z * b.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 ld3(const float* __restrict__ p) { return f3(__ldg(p), __ldg(p + 1), __ldg(p + 2)); }
+__device__ __forceinline__ void st3(float* p, float3 v) { p[0] = v.x; p[1] = v.y; p[2] = v.z; }
+__device__ __forceinline__ float comp(float3 v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : v.z); }
+
+// ------------------------------------------------------------------------------------------
+// Camera
+// ------------------------------------------------------------------------------------------
+// Camera-space direction through the centre of pixel (x, y); forward component is 1.
+__device__ __forceinline__ float3 pix_dir_cam(const DevCam& c, int x, int y) {
+  return f3(((float)x + 0.5f - c.cx) / c.f, -((float)y + 0.5f - c.cy) / c.f, -1.0f);
+}
+__device__ __forceinline__ float3 cam_to_world(const DevCam& c, float3 d) {
+  return f3(fmaf(c.R[0], d.x, fmaf(c.R[1], d.y, c.R[2] * d.z)), fmaf(c.R[3], d.x, fmaf(c.R[4], d.y, c.R[5] * d.z)),
+            fmaf(c.R[6], d.x, fmaf(c.R[7], d.y, c.R[8] * d.z)));
+}
+// World-space direction through the centre of pixel (x, y) (camera-space forward component 1;
+// the -1 z term is exact, so each component takes two roundings).
+__device__ __forceinline__ float3 pix_dir_world(const DevCam& c, int x, int y) {
+  const float dx = ((float)x + 0.5f - c.cx) / c.f, dy = -((float)y + 0.5f - c.cy) / c.f;
+  return f3(fmaf(c.R[0], dx, fmaf(c.R[1], dy, -c.R[2])), fmaf(c.R[3], dx, fmaf(c.R[4], dy, -c.R[5])),
+            fmaf(c.R[6], dx, fmaf(c.R[7], dy, -c.R[8])));
+}
+__device__ __forceinline__ float3 world_to_cam(const DevCam& c, float3 d) {
+  return f3(c.R[0] * d.x + c.R[3] * d.y + c.R[6] * d.z, c.R[1] * d.x + c.R[4] * d.y + c.R[7] * d.z,
+            c.R[2] * d.x + c.R[5] * d.y + c.R[8] * d.z);
+}
+__device__ __forceinline__ bool is_background(float z) { return !(isfinite(z) && z > 0.0f); }
+
+// ------------------------------------------------------------------------------------------
+// Philox4x32-10: ten rounds of the 4x32 S-box, multipliers 0xD2511F53 / 0xCD9E8D57 and key
+// increments 0x9E3779B9 / 0xBB67AE85 (Salmon, Moraes, Dror, Shaw 2011).
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// (xi0, xi1) of sample s at pixel `pix` of view `view`.
+__device__ __forceinline__ float2 sample_uniforms(uint64_t seed, int view, uint32_t pix, uint32_t s) {
+  const uint2 key = make_uint2((uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32) ^ (uint32_t)view);
+  const uint4 o = philox4x32_10(make_uint4(pix, s, 0u, 0u), key);
+  return make_float2((float)(o.x >> 8) * (1.0f / 16777216.0f), (float)(o.y >> 8) * (1.0f / 16777216.0f));
+}
+
+// ------------------------------------------------------------------------------------------
+// Microfacet terms (Appendix B); alpha = rho as printed.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float ggx_D(float nh, float rho) {
+  const float a2 = rho * rho;
+  const float den = nh * nh * (a2 - 1.0f) + 1.0f;
+  return a2 / (kPi * den * den);
+}
+__device__ __forceinline__ float ggx_G1(float z, float rho) {
+  const float a2 = rho * rho;
+  return 2.0f * z / (z + sqrtf(a2 + (1.0f - a2) * z * z));
+}
+__device__ __forceinline__ float pow5(float c) {
+  const float c2 = c * c;
+  return c2 * c2 * c;
+}
+__device__ __forceinline__ float f0_of(float a, float m) { return 0.04f * (1.0f - m) + a * m; }
+
+// GGX half vector around n (Walter et al. 2007 inversion; frame of Duff et al. 2017).
+// cos^2 = (1 - xi0) / den and sin^2 = rho^2 xi0 / den with den = 1 + (rho^2 - 1) xi0: the
+// same values as sqrt(1 - cos^2) without its cancellation for near-mirror lobes.  *ct
+// receives cos(theta_h) = n.h.
+__device__ __forceinline__ float3 ggx_sample_h(float3 n, float rho, float xi0, float xi1, float* ct_out = nullptr) {
+  const float a2 = rho * rho;
+  const float den = fmaf(a2 - 1.0f, xi0, 1.0f);
+  const float ct = sqrtf((1.0f - xi0) / den);
+  const float st = sqrtf(a2 * xi0 / den);
+  if (ct_out) *ct_out = ct;
+  float sp, cp;
+  sincospif(2.0f * xi1, &sp, &cp);
+  const float sgn = n.z >= 0.0f ? 1.0f : -1.0f;
+  const float aa = -1.0f / (sgn + n.z);
+  const float bb = n.x * n.y * aa;
+  const float3 t1 = f3(1.0f + sgn * n.x * n.x * aa, sgn * bb, -sgn * n.x);
+  const float3 t2 = f3(bb, sgn + n.y * n.y * aa, -n.y);
+  return t1 * (st * cp) + t2 * (st * sp) + n * ct;
+}
+
+struct Sample {
+  float3 h, w;
+  float vh, nh, nw;
+  bool valid;
+};
+
+// n.h is the sampled cosine and n.w = 2 (v.h)(n.h) - n.v (identities of w = 2 (v.h) h - v),
+// both better conditioned in FP32 than dot products with the rounded vectors.
+__device__ __forceinline__ Sample make_sample(float3 n, float3 v, float nv, float rho, float2 xi) {
+  Sample s;
+  s.h = ggx_sample_h(n, rho, xi.x, xi.y, &s.nh);
+  s.vh = dot3(v, s.h);
+  s.w = s.h * (2.0f * s.vh) - v;
+  s.nw = fmaf(2.0f * s.vh, s.nh, -nv);
+  s.valid = (nv > 0.0f) && (s.nw > 0.0f) && (s.vh > 0.0f) && (s.nh > 0.0f);
+  return s;
+}
+
+// ------------------------------------------------------------------------------------------
+// Environment lookup
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 dir_to_uv(float3 d) {
+  const float u = 0.5f + atan2f(d.x, -d.z) * kInv2Pi;
+  const float v = atan2f(sqrtf(d.x * d.x + d.z * d.z), d.y) * kInvPi;
+  return make_float2(u, v);
+}
+
+struct Taps {
+  int idx[4];  // float offsets of the four texels
+  float tx, ty;
+};
+
+// Octant-reduced angles of a direction: the texel coordinates x = u w - 0.5 and y = v h - 0.5
+// of the lat-long mapping are written as base + ang * scale with |ang| <= pi/4 and an exact
+// base, so the bilinear fractions keep full FP32 precision (a full-range atan2 near +-pi would
+// cost ~4e-5 texel at w = 512).  Same mapping as dir_to_uv.
+struct DirAngles {
+  float ax, bx;  // x = bx + ax * w / (2 pi)
+  float ay, by;  // y = by + ay * h / pi  (by in units of h: 0, 1/2 or 1)
+};
+
+__device__ __forceinline__ DirAngles dir_angles(float3 d) {
+  DirAngles r;
+  const float X = -d.z, Y = d.x;
+  if (fabsf(Y) <= X) {
+    r.bx = 0.5f;
+    r.ax = atan2f(Y, X);
+  } else if (Y > fabsf(X)) {
+    r.bx = 0.75f;
+    r.ax = atan2f(-X, Y);
+  } else if (-X >= fabsf(Y)) {
+    r.bx = 1.0f;
+    r.ax = atan2f(-Y, -X);
+  } else {
+    r.bx = 0.25f;
+    r.ax = atan2f(X, -Y);
+  }
+  const float q = sqrtf(d.x * d.x + d.z * d.z);
+  if (d.y >= q) {
+    r.by = 0.0f;
+    r.ay = atan2f(q, d.y);
+  } else if (-d.y >= q) {
+    r.by = 1.0f;
+    r.ay = -atan2f(q, -d.y);
+  } else {
+    r.by = 0.5f;
+    r.ay = -atan2f(d.y, q);
+  }
+  return r;
+}
+
+// integer part and fraction of base * n - 0.5 + ang * k
+__device__ __forceinline__ void split_coord(float base, float ang, int n, float k, int& i0, float& t) {
+  const float b = fmaf(base, (float)n, -0.5f);  // exact: n is a power of two
+  float f0 = floorf(fmaf(ang, k, b));
+  t = fmaf(ang, k, b - f0);
+  if (t < 0.0f) {
+    t += 1.0f;
+    f0 -= 1.0f;
+  } else if (t >= 1.0f) {
+    t -= 1.0f;
+    f0 += 1.0f;
+  }
+  i0 = (int)f0;
+}
+
+__device__ __forceinline__ Taps env_taps(const EnvInfo& e, int l, const DirAngles& a) {
+  Taps t;
+  const int h = e.h[l], w = e.w[l];
+  int x0, y0;
+  split_coord(a.bx, a.ax, w, (float)w * kInv2Pi, x0, t.tx);
+  split_coord(a.by, a.ay, h, (float)h * kInvPi, y0, t.ty);
+  int c0 = x0 % w;
+  if (c0 < 0) c0 += w;
+  int c1 = c0 + 1;
+  if (c1 >= w) c1 -= w;
+  const int r0 = min(max(y0, 0), h - 1), r1 = min(max(y0 + 1, 0), h - 1);
+  const int base = e.off[l];
+  t.idx[0] = base + (r0 * w + c0) * 3;
+  t.idx[1] = base + (r0 * w + c1) * 3;
+  t.idx[2] = base + (r1 * w + c0) * 3;
+  t.idx[3] = base + (r1 * w + c1) * 3;
+  return t;
+}
+
+__device__ __forceinline__ float3 bilinear(const float* __restrict__ mips, const Taps& t) {
+  const float3 a = ld3(mips + t.idx[0]), b = ld3(mips + t.idx[1]);
+  const float3 c = ld3(mips + t.idx[2]), d = ld3(mips + t.idx[3]);
+  const float w00 = (1.0f - t.tx) * (1.0f - t.ty), w01 = t.tx * (1.0f - t.ty);
+  const float w10 = (1.0f - t.tx) * t.ty, w11 = t.tx * t.ty;
+  return a * w00 + b * w01 + c * w10 + d * w11;
+}
+
+// SampleEnvMap(d, lambda): bilinear at floor(lambda) and the next level, blended linearly.
+__device__ __forceinline__ float3 env_lookup(const float* __restrict__ mips, const EnvInfo& e, float3 d, float lam) {
+  const float lmax = (float)(e.levels - 1);
+  lam = fminf(fmaxf(lam, 0.0f), lmax);
+  const int l0 = (int)floorf(lam);
+  const int l1 = min(l0 + 1, e.levels - 1);
+  const float t = lam - (float)l0;
+  const DirAngles ang = dir_angles(d);
+  const float3 a = bilinear(mips, env_taps(e, l0, ang));
+  if (t == 0.0f) return a;
+  const float3 b = bilinear(mips, env_taps(e, l1, ang));
+  return a * (1.0f - t) + b * t;
+}
+
+__device__ __forceinline__ float3 env_lookup0(const float* __restrict__ mips, const EnvInfo& e, float3 d) {
+  return bilinear(mips, env_taps(e, 0, dir_angles(d)));
+}
+
+// ------------------------------------------------------------------------------------------
+// BRDF table lookup: bilinear at texel centres, clamped.  Also returns d/drho, d/dmu of A, B
+// (zero where the coordinate is clamped).
+// ------------------------------------------------------------------------------------------
+struct LutVal {
+  float A, B, dA_drho, dB_drho, dA_dmu, dB_dmu;
+};
+
+__device__ __forceinline__ LutVal lut_sample(const float* __restrict__ lut, int N, float rho, float mu) {
+  LutVal r;
+  float x = mu * (float)N - 0.5f, y = rho * (float)N - 0.5f;
+  const bool xin = (x > 0.0f && x < (float)(N - 1)), yin = (y > 0.0f && y < (float)(N - 1));
+  x = fminf(fmaxf(x, 0.0f), (float)(N - 1));
+  y = fminf(fmaxf(y, 0.0f), (float)(N - 1));
+  const int x0 = min((int)floorf(x), N - 2), y0 = min((int)floorf(y), N - 2);
+  const float tx = x - (float)x0, ty = y - (float)y0;
+  const float2 v00 = __ldg(reinterpret_cast<const float2*>(lut) + (y0 * N + x0));
+  const float2 v01 = __ldg(reinterpret_cast<const float2*>(lut) + (y0 * N + x0 + 1));
+  const float2 v10 = __ldg(reinterpret_cast<const float2*>(lut) + ((y0 + 1) * N + x0));
+  const float2 v11 = __ldg(reinterpret_cast<const float2*>(lut) + ((y0 + 1) * N + x0 + 1));
+  r.A = (1 - ty) * ((1 - tx) * v00.x + tx * v01.x) + ty * ((1 - tx) * v10.x + tx * v11.x);
+  r.B = (1 - ty) * ((1 - tx) * v00.y + tx * v01.y) + ty * ((1 - tx) * v10.y + tx * v11.y);
+  const float fN = (float)N;
+  r.dA_dmu = xin ? fN * ((1 - ty) * (v01.x - v00.x) + ty * (v11.x - v10.x)) : 0.0f;
+  r.dB_dmu = xin ? fN * ((1 - ty) * (v01.y - v00.y) + ty * (v11.y - v10.y)) : 0.0f;
+  r.dA_drho = yin ? fN * ((1 - tx) * (v10.x - v00.x) + tx * (v11.x - v01.x)) : 0.0f;
+  r.dB_drho = yin ? fN * ((1 - tx) * (v10.y - v00.y) + tx * (v11.y - v01.y)) : 0.0f;
+  return r;
+}
+
+}  // namespace ssgi

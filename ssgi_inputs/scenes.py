@@ -131,6 +131,27 @@ def make_scene(seed: int, n_boxes: int, spread: float, n_mirrors: int = 0,
     return Scene(ground, ground_half, boxes, quads)
 
 
+def _screen_rect(cam: np.ndarray, H: int, W: int, lo, hi):
+    """Pixel slices covering the projection of the box [lo, hi] (the whole image if a corner
+    lies behind the camera).  Only narrows the search; every covered pixel is still ray-cast."""
+    c = cam.astype(np.float64)
+    m = c[:12].reshape(3, 4)
+    rot, eye = m[:, :3], m[:, 3]
+    f = (H / 2.0) / math.tan(c[12] / 2.0)
+    corners = np.array([[x, y, z] for x in (lo[0], hi[0]) for y in (lo[1], hi[1]) for z in (lo[2], hi[2])])
+    q = (corners - eye) @ rot
+    z = -q[:, 2]
+    if np.any(z <= 1e-3):
+        return slice(0, H), slice(0, W)
+    sx = W / 2.0 + f * q[:, 0] / z
+    sy = H / 2.0 - f * q[:, 1] / z
+    x0, x1 = int(max(0, math.floor(sx.min()) - 1)), int(min(W, math.ceil(sx.max()) + 1))
+    y0, y1 = int(max(0, math.floor(sy.min()) - 1)), int(min(H, math.ceil(sy.max()) + 1))
+    if x0 >= x1 or y0 >= y1:
+        return slice(0, 0), slice(0, 0)
+    return slice(y0, y1), slice(x0, x1)
+
+
 def raycast_gbuffer(scene: Scene, cam: np.ndarray, H: int, W: int) -> dict:
     """Ray-cast the analytic scene through the pixel centres of `cam` into an FP32 G-buffer.
 
@@ -161,18 +182,35 @@ def raycast_gbuffer(scene: Scene, cam: np.ndarray, H: int, W: int) -> dict:
             ok = (t > 1e-6) & (np.abs(p[..., 0]) <= scene.ground_half) & (np.abs(p[..., 2]) <= scene.ground_half)
             commit(np.where(ok, t, np.inf), np.array([0.0, 1.0, 0.0]), scene.ground)
         for b in scene.boxes:
-            t0 = (b.lo - eye) / d
-            t1 = (b.hi - eye) / d
+            ys, xs = _screen_rect(cam, H, W, b.lo, b.hi)
+            dd = d[ys, xs]
+            t0 = (b.lo - eye) / dd
+            t1 = (b.hi - eye) / dd
             tmin = np.minimum(t0, t1)
             tmax = np.maximum(t0, t1)
             t_in = tmin.max(axis=-1)
             t_out = tmax.min(axis=-1)
             ok = (t_in <= t_out) & (t_in > 1e-6)
             axis = tmin.argmax(axis=-1)
-            sign = -np.sign(np.take_along_axis(d, axis[..., None], axis=-1)[..., 0])
-            n = np.zeros((H, W, 3))
+            sign = -np.sign(np.take_along_axis(dd, axis[..., None], axis=-1)[..., 0])
+            n = np.zeros(dd.shape)
             np.put_along_axis(n, axis[..., None], sign[..., None], axis=-1)
-            commit(np.where(ok, t_in, np.inf), n, b.mat)
+            tb = t_best[ys, xs]
+            better = np.where(ok, t_in, np.inf) < tb
+            tb[better] = t_in[better]
+            t_best[ys, xs] = tb
+            sub = nrm[ys, xs]
+            sub[better] = n[better]
+            nrm[ys, xs] = sub
+            sub = alb[ys, xs]
+            sub[better] = b.mat.albedo
+            alb[ys, xs] = sub
+            sub = rough[ys, xs]
+            sub[better] = b.mat.rough
+            rough[ys, xs] = sub
+            sub = metal[ys, xs]
+            sub[better] = b.mat.metal
+            metal[ys, xs] = sub
         for q in scene.quads:
             nq = np.cross(q.axis_u, q.axis_v)
             denom = d @ nq

@@ -1,0 +1,80 @@
+"""CPU checks of the C ABI: libssgi.so builds, loads without a GPU, exports every function
+include/ssgi.h declares, and its host-side size queries and argument validation behave.
+No call here reaches a CUDA API (validation fails before any launch)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def N():
+    from paper_2504_01358_gb300 import _native
+    _native.lib()
+    return _native
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ssgi.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ssgi_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(N):
+    names = _declared()
+    assert len(names) >= 12
+    lib = C.CDLL(N.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(N.EXPORTED), set(names) - set(N.EXPORTED)
+
+
+def test_status_strings_and_version(N):
+    L = N.lib()
+    assert L.ssgi_status_string(0) == b"ok"
+    assert L.ssgi_status_string(1) == b"invalid argument"
+    assert b"sm_103a" in L.ssgi_version()
+
+
+def test_size_queries_match_the_oracle_layout(N):
+    L = N.lib()
+    for h, w in [(64, 128), (256, 512), (1, 2), (8, 8)]:
+        assert L.ssgi_env_levels(h, w) == O.env_levels(h, w)
+        assert L.ssgi_env_mip_floats(h, w) == O.build_env_mips(__import__("numpy").zeros((h, w, 3))).size
+    assert L.ssgi_env_levels(3, 8) == -1 and L.ssgi_env_levels(8, 4) == -1
+    for (V, H, W), lev in [((1, 900, 1600), 8), ((3, 37, 53), 6), ((1, 1, 1), 1)]:
+        assert L.ssgi_hiz_floats(N.Dims(V, H, W), lev) == V * O.hiz_floats_per_view(H, W, lev)
+    ws = L.ssgi_backward_workspace_bytes(N.Dims(1, 900, 1600), 256, 512)
+    assert ws >= 4 * (3 * 900 * 1600 + O.build_env_mips(__import__("numpy").zeros((256, 512, 3))).size)
+    assert L.ssgi_backward_workspace_bytes(N.Dims(0, 9, 9), 256, 512) == 0
+
+
+def test_invalid_arguments_fail_before_any_launch(N):
+    L = N.lib()
+    fake = C.c_void_p(0x100000)
+    assert L.ssgi_build_hiz(None, N.Dims(1, 8, 8), 4, fake, None) == 1
+    assert L.ssgi_build_hiz(fake, N.Dims(1, 8, 8), 0, fake, None) == 1
+    assert L.ssgi_build_hiz(fake, N.Dims(0, 8, 8), 4, fake, None) == 1
+    assert L.ssgi_build_env_mips(fake, 6, 8, fake, None) == 1
+    assert L.ssgi_build_brdf_lut(1, 64, fake, None) == 1
+    g = N.GBuffer(fake, fake, fake, fake, fake, N.Dims(1, 8, 8))
+    cam = (N.Camera * 1)()
+    cam[0].fov_y_rad, cam[0].z_near = 1.0, 0.01
+    env = N.EnvMap(fake, 8, 16, 4)
+    p = N.TraceParams(4, 32, 8, 0.05, 100.0, 1, 0)
+    bad_p = N.TraceParams(0, 32, 8, 0.05, 100.0, 1, 0)
+    assert L.ssgi_trace_indirect(C.byref(g), cam, fake, fake, fake, C.byref(env), C.byref(bad_p), None, None, fake,
+                                 None, None, None) == 1
+    bad_env = N.EnvMap(fake, 8, 16, 3)
+    assert L.ssgi_shade_direct(C.byref(g), cam, C.byref(bad_env), fake, 64, fake, None, fake, None) == 1
+    bad_cam = (N.Camera * 1)()
+    assert L.ssgi_shade_direct(C.byref(g), bad_cam, C.byref(env), fake, 64, fake, None, fake, None) == 1
+    # workspace too small
+    assert L.ssgi_backward(fake, C.byref(g), cam, fake, C.byref(env), fake, 64, fake, C.byref(p), fake, fake, fake,
+                           fake, fake, fake, 16, None) == 1
+    assert L.ssgi_l2_loss(fake, fake, 0, fake, None, None) == 1

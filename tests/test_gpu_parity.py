@@ -1,0 +1,237 @@
+"""GPU (libssgi.so through the C ABI) vs the FP64 oracle, element by element on the same seeded
+inputs.  Sizes span several tiles with ragged tails; config 2 runs at full size (1600x900,
+16 spp) in the bench's launch configuration and is checked on a pixel sample."""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import ssgi_inputs as si
+from parity import (GRAD_RTOL, affected_pixels, assert_forward_parity, assert_rgb, gpu_forward, orc_forward,
+                    pixel_rel_err)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import paper_2504_01358_gb300 as S
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return S
+
+
+@pytest.fixture(scope="module")
+def olut():
+    return O.build_lut()
+
+
+# --------------------------------------------------------------------------------------------
+# precomputation
+# --------------------------------------------------------------------------------------------
+def test_brdf_lut_matches_oracle(S, olut):
+    lut = S.ssgi_build_brdf_lut().cpu().numpy()
+    assert lut.shape == olut.shape
+    np.testing.assert_allclose(lut, olut, rtol=0, atol=2e-5)
+
+
+@pytest.mark.parametrize("hw", [(64, 128), (256, 512), (1, 4), (8, 8)])
+def test_env_mips_match_oracle(S, hw):
+    env = si.lognormal_env(11, *hw)
+    mips = S.ssgi_build_env_mips(torch.from_numpy(env).cuda()).mips.cpu().numpy()
+    ref = O.build_env_mips(env)
+    np.testing.assert_allclose(mips, ref, rtol=2e-6, atol=0)
+
+
+@pytest.mark.parametrize("shape,levels", [((1, 256, 256), 8), ((3, 37, 53), 6), ((2, 900, 1600), 8), ((1, 1, 1), 8),
+                                          ((1, 70, 33), 16)])
+def test_hiz_is_bitwise_equal(S, shape, levels):
+    rng = np.random.default_rng(sum(shape) + levels)
+    depth = rng.uniform(0.5, 50.0, size=shape).astype(np.float32)
+    depth[..., : shape[1] // 3, : shape[2] // 2] = np.inf
+    hiz = S.ssgi_build_hiz(torch.from_numpy(depth).cuda(), levels).cpu().numpy()
+    ref = O.build_hiz(depth, levels).astype(np.float32).reshape(-1)
+    assert hiz.size >= ref.size
+    assert np.array_equal(hiz[: ref.size], ref)
+
+
+# --------------------------------------------------------------------------------------------
+# forward
+# --------------------------------------------------------------------------------------------
+def test_shade_direct_matches_oracle(S, small, cfg1, olut):
+    for wl in (small, cfg1):
+        g = gpu_forward(wl)
+        r = orc_forward(wl, lut=olut)
+        for key in ("cd", "cs", "c1"):
+            assert_rgb(pixel_rel_err(g[key], r[key]).ravel(), f"{wl.name} {key}")
+
+
+@pytest.mark.parametrize("flags", [0, 1])
+def test_trace_matches_oracle_small(S, small, olut, flags):
+    g = gpu_forward(small, flags=flags)
+    r = orc_forward(small, lut=olut, flags=flags)
+    assert_forward_parity(g, r, f"small flags={flags}")
+
+
+def test_trace_matches_oracle_config1(S, cfg1, olut):
+    g = gpu_forward(cfg1)
+    r = orc_forward(cfg1, lut=olut)
+    frac, nbad = assert_forward_parity(g, r, "config1")
+    assert (g["hit_idx"] >= 0).sum() > 10000
+
+
+def test_trace_matches_oracle_multiview_ragged(S, olut):
+    scene = si.make_scene(21, 12, 4.0, 2)
+    cams = [si.look_at((5 * np.sin(a), 1.8, 5 * np.cos(a)), (0, 0.4, 0)) for a in (0.0, 2.1, 4.2)]
+    bufs = [si.raycast_gbuffer(scene, c, 75, 131) for c in cams]
+    st = lambda k: np.stack([b[k] for b in bufs])  # noqa: E731
+    wl = si.Workload("3view-75x131", st("depth"), st("normal"), st("albedo"), st("rough"), st("metal"),
+                     np.stack(cams), si.lognormal_env(22, 32, 64), si.TraceParams(spp=8, max_steps=48, seed=77))
+    g = gpu_forward(wl)
+    r = orc_forward(wl, lut=olut)
+    assert_forward_parity(g, r, "3 views")
+
+
+def test_brute_force_mode_matches_oracle(S, small, olut):
+    g = gpu_forward(small, brute=True)
+    r = orc_forward(small, lut=olut, brute=True)
+    assert_forward_parity(g, r, "brute force")
+
+
+def test_config2_full_size_sampled(S, olut):
+    """1600x900, 16 spp, 40 boxes + 2 mirrors, 64 steps -- the benchmark's launch -- against the
+    oracle on 30k sampled pixels (480k rays)."""
+    wl = si.config2()
+    g = gpu_forward(wl)
+    rng = np.random.default_rng(0)
+    V, H, W = wl.depth.shape
+    pl = np.sort(rng.choice(V * H * W, size=30000, replace=False))
+    r = O.forward(wl, lut=olut, pix_list=pl)
+    sub = {k: g[k].reshape((V * H * W,) + g[k].shape[3:])[pl] for k in ("hit_idx", "final", "cs_mc", "c_id")}
+    assert_forward_parity(sub, r, "config2 sample")
+    # the Hi-Z pyramid and direct pass at full size
+    assert np.array_equal(g["hiz"][: r["hiz"].size], r["hiz"].astype(np.float32).reshape(-1))
+    assert_rgb(pixel_rel_err(g["c1"], r["c1"]).ravel(), "config2 c1")
+    assert (sub["hit_idx"] >= 0).mean() > 0.05
+
+
+# --------------------------------------------------------------------------------------------
+# special cases
+# --------------------------------------------------------------------------------------------
+def test_zero_albedo_and_black_env_are_exactly_zero(S, small, olut):
+    wl = dataclasses.replace(small, albedo=np.zeros_like(small.albedo))
+    g = gpu_forward(wl, flags=1)
+    assert np.all(g["c_id"] == 0.0) and (g["hit_idx"] >= 0).any()
+    wl = dataclasses.replace(wl, env=np.zeros_like(small.env), metal=np.zeros_like(small.metal))
+    g = gpu_forward(wl, flags=1)
+    for k in ("cd", "cs", "c1", "cs_mc", "final", "c_id"):
+        assert np.all(g[k] == 0.0), k
+
+
+def test_fronto_parallel_plane_no_hits_on_gpu(S):
+    cam = si.look_at((0.0, 0.0, 0.0), (0.0, 0.0, -1.0))
+    q = si.Quad(np.array([0.0, 0.0, -3.0]), np.array([1.0, 0, 0]), np.array([0, 1.0, 0]), 50.0, 50.0,
+                si.Material((0.5, 0.6, 0.7), 0.6, 0.0))
+    gb = si.raycast_gbuffer(si.Scene(None, 0.0, [], [q]), cam, 64, 96)
+    wl = si.Workload("fronto", gb["depth"][None], gb["normal"][None], gb["albedo"][None], gb["rough"][None],
+                     gb["metal"][None], cam[None], si.lognormal_env(3, 16, 32), si.TraceParams(spp=8, max_steps=200))
+    g = gpu_forward(wl)
+    assert np.all(g["hit_idx"] < 0)
+
+
+@pytest.mark.parametrize("case", ["1x1", "all_background", "spp1", "steps0", "levels1", "odd"])
+def test_edge_cases_match_oracle(S, olut, case):
+    base = si.small_case(seed=5, H=37, W=53, spp=4)
+    p = base.params
+    if case == "1x1":
+        wl = dataclasses.replace(base, depth=base.depth[:, 30:31, 20:21].copy(), normal=base.normal[:, 30:31, 20:21].copy(),
+                                 albedo=base.albedo[:, 30:31, 20:21].copy(), rough=base.rough[:, 30:31, 20:21].copy(),
+                                 metal=base.metal[:, 30:31, 20:21].copy())
+    elif case == "all_background":
+        wl = dataclasses.replace(base, depth=np.full_like(base.depth, np.inf))
+    elif case == "spp1":
+        wl = dataclasses.replace(base, params=dataclasses.replace(p, spp=1))
+    elif case == "steps0":
+        wl = dataclasses.replace(base, params=dataclasses.replace(p, max_steps=0))
+    elif case == "levels1":
+        wl = dataclasses.replace(base, params=dataclasses.replace(p, hiz_levels=1))
+    else:
+        wl = dataclasses.replace(base, params=dataclasses.replace(p, spp=7, hiz_levels=3, max_steps=5))
+    g = gpu_forward(wl)
+    r = orc_forward(wl, lut=olut)
+    assert_forward_parity(g, r, case)
+    assert_rgb(pixel_rel_err(g["c1"], r["c1"]).ravel(), case)
+
+
+def test_invalid_arguments_are_rejected(S):
+    d = torch.zeros((1, 8, 8), device="cuda")
+    with pytest.raises(S._native.SSGIError):
+        S.ssgi_build_hiz(d, 99)
+    with pytest.raises(ValueError):
+        S.ssgi_build_env_mips(torch.zeros((3, 8, 3), device="cuda"))
+    with pytest.raises(ValueError):
+        S.ssgi_build_hiz(d.cpu(), 4)
+
+
+# --------------------------------------------------------------------------------------------
+# backward
+# --------------------------------------------------------------------------------------------
+def _backward_pair(S, wl, olut, flags):
+    g = gpu_forward(wl, flags=flags)
+    r = orc_forward(wl, lut=olut, flags=flags)
+    target = wl.target.astype(np.float64)
+    g_final = (2.0 * (r["final"] - target) / r["final"].size).astype(np.float32)
+    gb, env, cams, em, lut_t, c1, hit_idx, p = g["_dev"]
+    grads = S.ssgi_backward(torch.from_numpy(g_final).cuda(), gb, cams, c1, em, lut_t, hit_idx, p)
+    torch.cuda.synchronize()
+    ggpu = {k: v.cpu().numpy() for k, v in grads.items()}
+    He, We = wl.env.shape[:2]
+    gorc = O.backward(wl.depth, wl.normal, wl.albedo, wl.rough, wl.metal, wl.cams, r["mips"], He, We, olut, r["c1"],
+                      r["hit_idx"], g_final, wl.params.spp, wl.params.seed, flags)
+    aff = affected_pixels(g["hit_idx"], r["hit_idx"])
+    return ggpu, gorc, aff
+
+
+@pytest.mark.parametrize("flags", [0, 1])
+@pytest.mark.parametrize("name", ["small", "cfg1"])
+def test_backward_matches_oracle_adjoint(S, olut, request, name, flags):
+    wl = request.getfixturevalue(name)
+    if wl.target is None:
+        wl = dataclasses.replace(wl, target=si.uniform_target(99, *wl.depth.shape))
+    ggpu, gorc, aff = _backward_pair(S, wl, olut, flags)
+    ok = ~aff
+    for k in ("albedo", "rough", "metal", "normal"):
+        a, b = ggpu[k][ok], gorc[k][ok]
+        scale = np.abs(b).max()
+        err = np.abs(a - b).max() / scale
+        assert err <= GRAD_RTOL, (k, err)
+    a, b = ggpu["env"], gorc["env"]
+    rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+    assert rel <= GRAD_RTOL, ("env", rel)
+
+
+def test_autograd_function_matches_backward_call(S, small, olut):
+    wl = small
+    g, env, cams, tgt = S.to_device_workload(wl)
+    p = S.params_of(wl.params)
+    lut = S.ssgi_build_brdf_lut()
+    leaves = {k: getattr(g, k).clone().requires_grad_(True) for k in ("normal", "albedo", "rough", "metal")}
+    env_l = env.clone().requires_grad_(True)
+    final = S.ssgi_render(g.depth, leaves["normal"], leaves["albedo"], leaves["rough"], leaves["metal"], env_l, cams,
+                          p, lut)
+    loss = ((final - tgt) ** 2).mean()
+    loss.backward()
+    # same through the explicit calls
+    em = S.ssgi_build_env_mips(env)
+    hiz = S.ssgi_build_hiz(g.depth, p.hiz_levels)
+    c_d, _, c1 = S.ssgi_shade_direct(g, cams, em, lut)
+    tr = S.ssgi_trace_indirect(g, cams, hiz, c1, c_d, em, p, want_hits=True)
+    gf, _ = S.ssgi_l2_loss(tr["final"], tgt)
+    gr = S.ssgi_backward(gf, g, cams, c1, em, lut, tr["hit_idx"], p)
+    torch.cuda.synchronize()
+    for k in ("normal", "albedo", "rough", "metal"):
+        a, b = leaves[k].grad.cpu().numpy(), gr[k].cpu().numpy()
+        assert np.abs(a - b).max() <= 1e-5 * max(np.abs(b).max(), 1e-12), k
+    a, b = env_l.grad.cpu().numpy(), gr["env"].cpu().numpy()
+    assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max()
