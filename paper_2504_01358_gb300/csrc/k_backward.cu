@@ -39,10 +39,28 @@ struct BwdArgs {
   uint32_t flags;
 };
 
+// Warp-aggregated float3 atomic add: lanes of the calling (possibly partial) warp that
+// target the same address are summed by shuffles and one lane issues the atomics.  Many
+// pixels hit the same texels (a floor's normal always looks up the same polar texels, coarse
+// mips have a handful of texels), and plain atomics on one address serialise in L2.
 __device__ __forceinline__ void atomic_add3(float* p, float3 v) {
-  atomicAdd(p + 0, v.x);
-  atomicAdd(p + 1, v.y);
-  atomicAdd(p + 2, v.z);
+  const unsigned act = __activemask();
+  const unsigned grp = __match_any_sync(act, (unsigned long long)p);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(grp) - 1;
+  unsigned rest = grp & ~(1u << leader);
+  float3 s = v;
+  while (rest) {
+    const int src = __ffs(rest) - 1;
+    rest &= rest - 1;
+    const float tx = __shfl_sync(grp, v.x, src), ty = __shfl_sync(grp, v.y, src), tz = __shfl_sync(grp, v.z, src);
+    if (lane == leader) s = s + f3(tx, ty, tz);
+  }
+  if (lane == leader) {
+    atomicAdd(p + 0, s.x);
+    atomicAdd(p + 1, s.y);
+    atomicAdd(p + 2, s.z);
+  }
 }
 
 // d ln G1(z; rho) / dz, / drho

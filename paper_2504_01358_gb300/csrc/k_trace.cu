@@ -49,42 +49,47 @@ struct TraceArgs {
 constexpr int kTileW = 8;   // a warp covers an 8 x 4 pixel tile
 constexpr int kTileH = 16;  // a 128-thread block covers 8 x 16 pixels
 
-struct Seg {
-  float P0x, P0y, Dx, Dy, iDx, iDy;
+// One ray's march state.  The segment constants give the exit parameter of a cell edge bx as
+// s_x = bx * iDx + ox (iDx = 0, ox = +inf when the segment has no x extent), so an iteration
+// needs one FMA per axis; za caches the depth at the current parameter s.
+struct Ray {
+  float Dx, Dy, iDx, iDy, ox, oy, k0, dk, P0x, P0y;
+  float s, za;
+  int ix, iy, L;
 };
 
-// Exit parameters of the level-L cell holding pixel (ix, iy) through its x and y sides.
-__device__ __forceinline__ void cell_exit(const Seg& g, int ix, int iy, int L, float& sx, float& sy) {
-  const int S = 1 << L;
-  const int cxl = ix >> L, cyl = iy >> L;
-  sx = INFINITY;
-  sy = INFINITY;
-  if (g.Dx != 0.0f) sx = ((float)(g.Dx > 0.0f ? (cxl + 1) * S : cxl * S) - g.P0x) * g.iDx;
-  if (g.Dy != 0.0f) sy = ((float)(g.Dy > 0.0f ? (cyl + 1) * S : cyl * S) - g.P0y) * g.iDy;
+// Exit parameters of the level-L cell holding (ix, iy).
+__device__ __forceinline__ void exits(const Ray& r, float& sx, float& sy) {
+  const int bx = ((r.ix >> r.L) + (r.Dx > 0.0f ? 1 : 0)) << r.L;
+  const int by = ((r.iy >> r.L) + (r.Dy > 0.0f ? 1 : 0)) << r.L;
+  sx = fmaf((float)bx, r.iDx, r.ox);
+  sy = fmaf((float)by, r.iDy, r.oy);
 }
 
-// Move (ix, iy) to the pixel entered when the ray leaves the level-L cell.
-__device__ __forceinline__ void cell_step(const Seg& g, int L, float sx, float sy, int& ix, int& iy, float& s) {
-  const int S = 1 << L;
-  const int cxl = ix >> L, cyl = iy >> L;
+// Enter the pixel across the exit side of the level-L cell (ties go to x), on the row (column)
+// of the exit point clamped to the cell.
+__device__ __forceinline__ void step_out(Ray& r, float sx, float sy) {
+  const int lo_x = (r.ix >> r.L) << r.L, lo_y = (r.iy >> r.L) << r.L;
+  const int S1 = (1 << r.L) - 1;
   if (sx <= sy) {
-    const float fy = fminf(fmaxf(floorf(fmaf(sx, g.Dy, g.P0y)), (float)(cyl * S)), (float)(cyl * S + S - 1));
-    ix = g.Dx > 0.0f ? (cxl + 1) * S : cxl * S - 1;
-    iy = (int)fy;
-    s = sx;
+    const float fy = fminf(fmaxf(floorf(fmaf(sx, r.Dy, r.P0y)), (float)lo_y), (float)(lo_y + S1));
+    r.ix = r.Dx > 0.0f ? lo_x + S1 + 1 : lo_x - 1;
+    r.iy = (int)fy;
+    r.s = sx;
   } else {
-    const float fx = fminf(fmaxf(floorf(fmaf(sy, g.Dx, g.P0x)), (float)(cxl * S)), (float)(cxl * S + S - 1));
-    iy = g.Dy > 0.0f ? (cyl + 1) * S : cyl * S - 1;
-    ix = (int)fx;
-    s = sy;
+    const float fx = fminf(fmaxf(floorf(fmaf(sy, r.Dx, r.P0x)), (float)lo_x), (float)(lo_x + S1));
+    r.iy = r.Dy > 0.0f ? lo_y + S1 + 1 : lo_y - 1;
+    r.ix = (int)fx;
+    r.s = sy;
   }
 }
 
-// March from pixel (x, y) at linear depth z0 along camera-space direction w.  Returns the
-// hit pixel's index within the view, or SSGI_HIT_MISS.
+// March from pixel (x, y) at linear depth z0 (k0 = 1/z0) along camera-space direction w.
+// Returns the hit pixel's index within the view, or SSGI_HIT_MISS; `it` gets the iterations.
 __device__ __forceinline__ int march(const TraceArgs& A, const DevCam& c, const float* __restrict__ dep,
-                                     const float* __restrict__ hz_v, int levels, int max_steps, int x, int y,
-                                     float z0, float3 w, int& it) {
+                                     const float* __restrict__ hz_v, const int* __restrict__ s_hoff,
+                                     const int* __restrict__ s_hw, int levels, int max_steps, int x, int y,
+                                     float z0, float k0, float3 w, int& it) {
   const int H = A.vs.H, W = A.vs.W;
   it = 0;
   const float3 o = pix_dir_cam(c, x, y) * z0;
@@ -94,48 +99,62 @@ __device__ __forceinline__ int march(const TraceArgs& A, const DevCam& c, const 
   if (!(t_end > 0.0f)) return SSGI_HIT_MISS;
   const float3 X1 = o + w * t_end;
   const float z1 = -X1.z;
-  Seg g;
-  g.P0x = (float)x + 0.5f;
-  g.P0y = (float)y + 0.5f;
-  g.Dx = (c.cx + c.f * X1.x / z1) - g.P0x;
-  g.Dy = (c.cy - c.f * X1.y / z1) - g.P0y;
-  g.iDx = 1.0f / g.Dx;
-  g.iDy = 1.0f / g.Dy;
-  const float k0 = 1.0f / z0, dk = 1.0f / z1 - k0;
-
-  int ix = x, iy = y;
-  float s = 0.0f, sx, sy;
-  cell_exit(g, ix, iy, 0, sx, sy);  // leave the origin pixel untested
+  Ray r;
+  r.P0x = (float)x + 0.5f;
+  r.P0y = (float)y + 0.5f;
+  r.Dx = (c.cx + c.f * X1.x / z1) - r.P0x;
+  r.Dy = (c.cy - c.f * X1.y / z1) - r.P0y;
+  r.iDx = r.Dx != 0.0f ? 1.0f / r.Dx : 0.0f;
+  r.iDy = r.Dy != 0.0f ? 1.0f / r.Dy : 0.0f;
+  r.ox = r.Dx != 0.0f ? -r.P0x * r.iDx : INFINITY;
+  r.oy = r.Dy != 0.0f ? -r.P0y * r.iDy : INFINITY;
+  r.k0 = k0;
+  r.dk = 1.0f / z1 - k0;
+  r.ix = x;
+  r.iy = y;
+  r.L = 0;
+  float sx, sy;
+  exits(r, sx, sy);  // leave the origin pixel untested
   if (!(fminf(sx, sy) < 1.0f)) return SSGI_HIT_MISS;
-  cell_step(g, 0, sx, sy, ix, iy, s);
+  step_out(r, sx, sy);
+  r.za = 1.0f / fmaf(r.s, r.dk, r.k0);
 
-  int L = 0;
-  for (it = 0;; ++it) {
-    if (ix < 0 || ix >= W || iy < 0 || iy >= H) return SSGI_HIT_MISS;
-    if (it >= max_steps) return SSGI_HIT_MISS;
-    cell_exit(g, ix, iy, L, sx, sy);
+  for (;;) {
+    if (r.ix < 0 || r.ix >= W || r.iy < 0 || r.iy >= H || it >= max_steps) return SSGI_HIT_MISS;
+    ++it;
+    exits(r, sx, sy);
     const float se = fminf(sx, sy);
-    const float sb = fminf(se, 1.0f);
-    const float za = 1.0f / fmaf(s, dk, k0), zb = 1.0f / fmaf(sb, dk, k0);
-    const float zlo = fminf(za, zb), zhi = fmaxf(za, zb);
-    const float hzv = (L == 0) ? __ldg(dep + iy * W + ix)
-                               : __ldg(hz_v + A.hz.off[L] + (iy >> L) * A.hz.w[L] + (ix >> L));
+    const float zb = 1.0f / fmaf(fminf(se, 1.0f), r.dk, r.k0);
+    const float zlo = fminf(r.za, zb), zhi = fmaxf(r.za, zb);
+    const float hzv = (r.L == 0) ? __ldg(dep + r.iy * W + r.ix)
+                                 : __ldg(hz_v + s_hoff[r.L] + (r.iy >> r.L) * s_hw[r.L] + (r.ix >> r.L));
     if (zhi < hzv) {
       if (!(se < 1.0f)) return SSGI_HIT_MISS;
-      cell_step(g, L, sx, sy, ix, iy, s);
-      if (L + 1 < levels) ++L;
-    } else if (L > 0) {
-      --L;
+      step_out(r, sx, sy);
+      r.za = zb;
+      if (r.L + 1 < levels) ++r.L;
+    } else if (r.L > 0) {
+      --r.L;
     } else if (zlo <= hzv + A.thickness) {
-      return iy * W + ix;
+      return r.iy * W + r.ix;
     } else {
       if (!(se < 1.0f)) return SSGI_HIT_MISS;
-      cell_step(g, 0, sx, sy, ix, iy, s);
+      step_out(r, sx, sy);
+      r.za = zb;
     }
   }
 }
 
-__global__ void __launch_bounds__(128) k_trace(TraceArgs A) {
+// One thread per pixel, looping over its samples; a warp covers an 8 x 4 tile so that its
+// rays start close together and touch the same pyramid cells.
+template <bool kCid>
+__global__ void __launch_bounds__(kTileW * kTileH, 6) k_trace(TraceArgs A) {
+  __shared__ int s_hoff[SSGI_MAX_HIZ_LEVELS], s_hw[SSGI_MAX_HIZ_LEVELS];
+  if (threadIdx.x < SSGI_MAX_HIZ_LEVELS) {
+    s_hoff[threadIdx.x] = A.hz.off[threadIdx.x];
+    s_hw[threadIdx.x] = A.hz.w[threadIdx.x];
+  }
+  __syncthreads();
   const int W = A.vs.W, H = A.vs.H;
   const int x = blockIdx.x * kTileW + (threadIdx.x % kTileW);
   const int y = blockIdx.y * kTileH + (threadIdx.x / kTileW);
@@ -170,7 +189,7 @@ __global__ void __launch_bounds__(128) k_trace(TraceArgs A) {
   const float3 a = ld3(A.albedo + 3 * p);
   const float3 F0 = f3(f0_of(a.x, m), f0_of(a.y, m), f0_of(a.z, m));
   const float g1v = ggx_G1(nv, rho);
-  const bool want_cid = (A.flags & SSGI_DIFFUSE_INDIRECT) != 0;
+  const float k0 = 1.0f / z0;
   float3 acc = f3(0.f, 0.f, 0.f), accd = f3(0.f, 0.f, 0.f);
   unsigned long long steps = 0;
 
@@ -180,24 +199,25 @@ __global__ void __launch_bounds__(128) k_trace(TraceArgs A) {
     int q = SSGI_HIT_INVALID;
     if (sm.valid) {
       int it;
-      q = march(A, cam, dep, hz_v, levels, max_steps, x, y, z0, world_to_cam(cam, sm.w), it);
+      q = march(A, cam, dep, hz_v, s_hoff, s_hw, levels, max_steps, x, y, z0, k0, world_to_cam(cam, sm.w), it);
       steps += (unsigned long long)it;
       const float3 Li = q >= 0 ? ld3(A.c1 + 3 * (view * HW + q)) : env_lookup0(A.mips, A.e, sm.w);
       const float K = ggx_G1(sm.nw, rho) * g1v * sm.vh / (nv * sm.nh);
       const float fc = pow5(1.0f - sm.vh);
       const float3 F = F0 + (f3(1.f, 1.f, 1.f) - F0) * fc;
       acc = acc + mul3(F, Li) * K;
-      if (want_cid) {
+      if (kCid) {
         const float pdf = ggx_D(sm.nh, rho) * sm.nh / (4.0f * sm.vh);
         if (pdf > 0.0f && isfinite(pdf)) accd = accd + mul3(a, Li) * ((1.0f - m) * kInvPi * sm.nw / pdf);
       }
     }
     if (A.hit_idx) A.hit_idx[p * spp + s] = q;
   }
-  const float3 csm = f3(acc.x / (float)spp, acc.y / (float)spp, acc.z / (float)spp);
-  const float3 cid = f3(accd.x / (float)spp, accd.y / (float)spp, accd.z / (float)spp);
+  const float fs = (float)spp;
+  const float3 csm = f3(acc.x / fs, acc.y / fs, acc.z / fs);
+  const float3 cid = f3(accd.x / fs, accd.y / fs, accd.z / fs);
   float3 fin = ld3(A.c_d + 3 * p) + csm;
-  if (want_cid) fin = fin + cid;
+  if (kCid) fin = fin + cid;
   st3(A.final_out + 3 * p, fin);
   if (A.c_s_mc) st3(A.c_s_mc + 3 * p, csm);
   if (A.c_id) st3(A.c_id + 3 * p, cid);
@@ -241,6 +261,9 @@ extern "C" ssgi_status ssgi_trace_indirect(const ssgi_gbuffer* g, const ssgi_cam
   A.seed = p->seed;
   A.flags = p->flags;
   dim3 grid(ceil_div(g->d.width, kTileW), ceil_div(g->d.height, kTileH), g->d.views);
-  k_trace<<<grid, kTileW * kTileH, 0, (cudaStream_t)stream>>>(A);
+  if (p->flags & SSGI_DIFFUSE_INDIRECT)
+    k_trace<true><<<grid, kTileW * kTileH, 0, (cudaStream_t)stream>>>(A);
+  else
+    k_trace<false><<<grid, kTileW * kTileH, 0, (cudaStream_t)stream>>>(A);
   return launch_status();
 }
