@@ -202,6 +202,34 @@ ssgi_status ssgi_backward(const float *g_final, const ssgi_gbuffer *g, const ssg
                           const ssgi_trace_params *p, float *g_albedo, float *g_rough, float *g_metal,
                           float *g_normal, float *g_env, void *workspace, size_t ws_bytes, ssgi_stream_t stream);
 
+/* ---------------------------------------------------------------------------------------- */
+/* Allocation-free backward (no counterpart in the paper; an interface convenience)          */
+/* ---------------------------------------------------------------------------------------- */
+/* Largest scratch the allocation-free backward can use: 32 MiB.  That covers one 1600x900
+ * view with a 256x512 environment (19.4 MB); see ssgi_backward_workspace_bytes. */
+#define SSGI_BACKWARD_NOALLOC_MAX_BYTES (32u << 20)
+
+/* Same computation, arguments and outputs as ssgi_backward, for callers that cannot allocate
+ * device memory while they run -- a render or training loop held to a fixed per-frame memory
+ * budget, a host application whose pool allocator owns all device memory, or code running where
+ * a cudaMalloc would synchronise the device and stall other streams.  Instead of a caller
+ * workspace it uses a scratch array of SSGI_BACKWARD_NOALLOC_MAX_BYTES that lives in the
+ * library's device image: every GPU that loads the library keeps that memory until the process
+ * exits.  It calls no cudaMalloc or cudaFree and no allocating library routine.
+ *   - The first call on a device looks up that device's address of the array (with that device
+ *     current); make that first call before any stream capture.
+ *   - Sizes whose workspace (ssgi_backward_workspace_bytes) exceeds the maximum return
+ *     SSGI_ERR_UNSUPPORTED before anything is enqueued.
+ *   - The scratch is cleared on `stream` at the start of every call and keeps the last call's
+ *     contents afterwards.  All calls on a device share it: calls that may overlap on the GPU
+ *     (different streams without ordering between them) race and give wrong results; order them
+ *     on one stream or with events. */
+ssgi_status ssgi_backward_noalloc(const float *g_final, const ssgi_gbuffer *g, const ssgi_camera *cams,
+                                  const float *c1, const ssgi_envmap *env, const float *lut, int32_t lut_n,
+                                  const int32_t *hit_idx, const ssgi_trace_params *p, float *g_albedo,
+                                  float *g_rough, float *g_metal, float *g_normal, float *g_env,
+                                  ssgi_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,6 +12,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libssgi.so")
 
 SSGI_MAX_VIEWS = 32
+BACKWARD_NOALLOC_MAX_BYTES = 32 << 20
 HIT_MISS, HIT_INVALID, HIT_BACKGROUND = -1, -2, -3
 DIFFUSE_INDIRECT = 1
 BRUTE_FORCE = 2
@@ -73,6 +74,8 @@ _SIGS = {
     "ssgi_l2_loss": (C.c_int, [VP, VP, I64, VP, VP, VP]),
     "ssgi_backward": (C.c_int, [VP, C.POINTER(GBuffer), C.POINTER(Camera), VP, C.POINTER(EnvMap), VP, I32, VP,
                                 C.POINTER(TraceParams), VP, VP, VP, VP, VP, VP, SZ, VP]),
+    "ssgi_backward_noalloc": (C.c_int, [VP, C.POINTER(GBuffer), C.POINTER(Camera), VP, C.POINTER(EnvMap), VP, I32,
+                                        VP, C.POINTER(TraceParams), VP, VP, VP, VP, VP, VP]),
 }
 
 # every symbol include/ssgi.h declares (checked by the CPU tests)

@@ -11,6 +11,8 @@
 //                 c_s = L_E(r, lambda) (F0 A + B) with d/dc_d = g_final + g_c1, d/dc_s = g_c1;
 //   k_bwd_env     per base texel: adjoint of the 2x2 box mip chain (each level-l ancestor
 //                 contributes its gradient / 4^l).
+#include <mutex>
+
 #include "ssgi_device.cuh"
 
 namespace ssgi {
@@ -372,3 +374,85 @@ ssgi_status ssgi_backward(const float* g_final, const ssgi_gbuffer* g, const ssg
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free backward: the workspace is a fixed array in the library's device image, so
+// callers that must not allocate device memory can still run the adjoint.  Device code could
+// name the array directly; host code needs its device address, looked up once per device.
+// ------------------------------------------------------------------------------------------
+namespace ssgi {
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SSGI_BACKWARD_NOALLOC_MAX_BYTES];
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (first call per device looks it
+// up with that device current).
+ssgi_status noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SSGI_ERR_CUDA;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return SSGI_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return SSGI_ERR_CUDA;
+    g_noalloc_addr[dev] = ptr;
+  }
+  *out = g_noalloc_addr[dev];
+  return SSGI_OK;
+}
+}  // namespace
+}  // namespace ssgi
+
+extern "C" ssgi_status ssgi_backward_noalloc(const float* g_final, const ssgi_gbuffer* g, const ssgi_camera* cams,
+                                             const float* c1, const ssgi_envmap* env, const float* lut,
+                                             int32_t lut_n, const int32_t* hit_idx, const ssgi_trace_params* p,
+                                             float* g_albedo, float* g_rough, float* g_metal, float* g_normal,
+                                             float* g_env, ssgi_stream_t stream) {
+  if (!g_final || gbuffer_ok(g) != SSGI_OK || trace_params_ok(p) != SSGI_OK || !c1 || !lut || lut_n < 2 ||
+      !hit_idx || !g_albedo || !g_rough || !g_metal || !g_normal || !g_env)
+    return SSGI_ERR_INVALID_ARG;
+  BwdArgs A;
+  if (make_views(cams, g->d, &A.vs) != SSGI_OK || make_env(env, &A.e) != SSGI_OK) return SSGI_ERR_INVALID_ARG;
+  const size_t need = ssgi_backward_workspace_bytes(g->d, env->h, env->w);
+  if (need == 0) return SSGI_ERR_INVALID_ARG;
+  if (need > (size_t)SSGI_BACKWARD_NOALLOC_MAX_BYTES) return SSGI_ERR_UNSUPPORTED;
+  void* workspace = nullptr;
+  const ssgi_status ss = noalloc_scratch(&workspace);
+  if (ss != SSGI_OK) return ss;
+  const long long npx = (long long)g->d.views * g->d.height * g->d.width;
+  const size_t c1_bytes = ((size_t)npx * 3 * sizeof(float) + 255) & ~(size_t)255;
+  A.g_c1 = (float*)workspace;
+  A.g_mips = (float*)((char*)workspace + c1_bytes);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(workspace, 0, need, s) != cudaSuccess) return SSGI_ERR_CUDA;
+  A.g_final = g_final;
+  A.depth = g->depth;
+  A.normal = g->normal;
+  A.albedo = g->albedo;
+  A.rough = g->rough;
+  A.metal = g->metal;
+  A.c1 = c1;
+  A.mips = env->mips;
+  A.lut = lut;
+  A.hit_idx = hit_idx;
+  A.g_albedo = g_albedo;
+  A.g_rough = g_rough;
+  A.g_metal = g_metal;
+  A.g_normal = g_normal;
+  A.lut_n = lut_n;
+  A.spp = p->spp;
+  A.seed = p->seed;
+  A.flags = p->flags;
+  const int blocks = ceil_div(npx, 256);
+  k_bwd_mc<<<blocks, 256, 0, s>>>(A);
+  ssgi_status st = launch_status();
+  if (st != SSGI_OK) return st;
+  k_bwd_direct<<<blocks, 256, 0, s>>>(A);
+  st = launch_status();
+  if (st != SSGI_OK) return st;
+  const int nt = env->h * env->w * 3;
+  k_bwd_env<<<ceil_div(nt, 256), 256, 0, s>>>(A.e, A.g_mips, g_env);
+  return launch_status();
+}

@@ -227,6 +227,20 @@ def ssgi_backward(g_final: torch.Tensor, g: GBuffer, cams, c1: torch.Tensor, env
     return out
 
 
+def ssgi_backward_noalloc(g_final: torch.Tensor, g: GBuffer, cams, c1: torch.Tensor, env: EnvMap,
+                          lut: torch.Tensor, hit_idx: torch.Tensor, params: TraceParams, out: dict,
+                          stream=None) -> dict:
+    """ssgi_backward without a workspace argument: the library's built-in scratch array is used,
+    for callers that cannot allocate device memory (outputs in `out` are still the caller's)."""
+    cam = cams if isinstance(cams, C.Array) else cameras(cams)
+    gs, es, ps = g.c_struct(), env.c_struct(), params.c_struct()
+    N.call("ssgi_backward_noalloc", _dev(g_final, "g_final"), C.byref(gs), cam, _dev(c1, "c1"), C.byref(es),
+           _dev(lut, "lut"), int(lut.shape[0]), _dev(hit_idx, "hit_idx", torch.int32), C.byref(ps),
+           _dev(out["albedo"], "g_albedo"), _dev(out["rough"], "g_rough"), _dev(out["metal"], "g_metal"),
+           _dev(out["normal"], "g_normal"), _dev(out["env"], "g_env"), _stream(stream))
+    return out
+
+
 # ------------------------------------------------------------------------------------------
 # autograd
 # ------------------------------------------------------------------------------------------
