@@ -50,20 +50,21 @@ constexpr int kTileW = 8;   // a warp covers an 8 x 4 pixel tile
 constexpr int kTileH = 16;  // a 128-thread block covers 8 x 16 pixels
 
 // One ray's march state.  The segment constants give the exit parameter of a cell edge bx as
-// s_x = bx * iDx + ox (iDx = 0, ox = +inf when the segment has no x extent), so an iteration
-// needs one FMA per axis; za caches the depth at the current parameter s.
+// s_x = bx * iDx + ox (iDx = 0, ox = +inf when the segment has no x extent).  Depth is handled
+// as k = 1/z, which is linear in the screen parameter, and the tests are written on k:
+//   z_hi < hz          <=>  k_min * hz > 1
+//   z_lo <= hz + thick <=>  k_max * (hz + thick) >= 1
+// (k > 0 on the clipped segment), so an iteration has no division; ka caches k at the cell
+// entry.
 struct Ray {
-  float Dx, Dy, iDx, iDy, ox, oy, k0, dk, P0x, P0y;
-  float s, za;
-  int ix, iy, L;
+  float P0x, P0y, Dx, Dy, iDx, iDy, ox, oy, k0, dk, ka;
+  int ix, iy, L, sgx, sgy;
 };
 
 // Exit parameters of the level-L cell holding (ix, iy).
 __device__ __forceinline__ void exits(const Ray& r, float& sx, float& sy) {
-  const int bx = ((r.ix >> r.L) + (r.Dx > 0.0f ? 1 : 0)) << r.L;
-  const int by = ((r.iy >> r.L) + (r.Dy > 0.0f ? 1 : 0)) << r.L;
-  sx = fmaf((float)bx, r.iDx, r.ox);
-  sy = fmaf((float)by, r.iDy, r.oy);
+  sx = fmaf((float)(((r.ix >> r.L) + r.sgx) << r.L), r.iDx, r.ox);
+  sy = fmaf((float)(((r.iy >> r.L) + r.sgy) << r.L), r.iDy, r.oy);
 }
 
 // Enter the pixel across the exit side of the level-L cell (ties go to x), on the row (column)
@@ -72,15 +73,13 @@ __device__ __forceinline__ void step_out(Ray& r, float sx, float sy) {
   const int lo_x = (r.ix >> r.L) << r.L, lo_y = (r.iy >> r.L) << r.L;
   const int S1 = (1 << r.L) - 1;
   if (sx <= sy) {
-    const float fy = fminf(fmaxf(floorf(fmaf(sx, r.Dy, r.P0y)), (float)lo_y), (float)(lo_y + S1));
-    r.ix = r.Dx > 0.0f ? lo_x + S1 + 1 : lo_x - 1;
-    r.iy = (int)fy;
-    r.s = sx;
+    const int fy = __float2int_rd(fmaf(sx, r.Dy, r.P0y));
+    r.iy = min(max(fy, lo_y), lo_y + S1);
+    r.ix = r.sgx ? lo_x + S1 + 1 : lo_x - 1;
   } else {
-    const float fx = fminf(fmaxf(floorf(fmaf(sy, r.Dx, r.P0x)), (float)lo_x), (float)(lo_x + S1));
-    r.iy = r.Dy > 0.0f ? lo_y + S1 + 1 : lo_y - 1;
-    r.ix = (int)fx;
-    r.s = sy;
+    const int fx = __float2int_rd(fmaf(sy, r.Dx, r.P0x));
+    r.ix = min(max(fx, lo_x), lo_x + S1);
+    r.iy = r.sgy ? lo_y + S1 + 1 : lo_y - 1;
   }
 }
 
@@ -108,6 +107,8 @@ __device__ __forceinline__ int march(const TraceArgs& A, const DevCam& c, const 
   r.iDy = r.Dy != 0.0f ? 1.0f / r.Dy : 0.0f;
   r.ox = r.Dx != 0.0f ? -r.P0x * r.iDx : INFINITY;
   r.oy = r.Dy != 0.0f ? -r.P0y * r.iDy : INFINITY;
+  r.sgx = r.Dx > 0.0f ? 1 : 0;
+  r.sgy = r.Dy > 0.0f ? 1 : 0;
   r.k0 = k0;
   r.dk = 1.0f / z1 - k0;
   r.ix = x;
@@ -115,32 +116,34 @@ __device__ __forceinline__ int march(const TraceArgs& A, const DevCam& c, const 
   r.L = 0;
   float sx, sy;
   exits(r, sx, sy);  // leave the origin pixel untested
-  if (!(fminf(sx, sy) < 1.0f)) return SSGI_HIT_MISS;
+  const float s0 = fminf(sx, sy);
+  if (!(s0 < 1.0f)) return SSGI_HIT_MISS;
   step_out(r, sx, sy);
-  r.za = 1.0f / fmaf(r.s, r.dk, r.k0);
+  r.ka = fmaf(s0, r.dk, r.k0);
+  const float thick = A.thickness;
 
   for (;;) {
-    if (r.ix < 0 || r.ix >= W || r.iy < 0 || r.iy >= H || it >= max_steps) return SSGI_HIT_MISS;
+    if ((unsigned)r.ix >= (unsigned)W || (unsigned)r.iy >= (unsigned)H || it >= max_steps) return SSGI_HIT_MISS;
     ++it;
     exits(r, sx, sy);
     const float se = fminf(sx, sy);
-    const float zb = 1.0f / fmaf(fminf(se, 1.0f), r.dk, r.k0);
-    const float zlo = fminf(r.za, zb), zhi = fmaxf(r.za, zb);
+    const float kb = fmaf(fminf(se, 1.0f), r.dk, r.k0);
+    const float kmin = fminf(r.ka, kb), kmax = fmaxf(r.ka, kb);
     const float hzv = (r.L == 0) ? __ldg(dep + r.iy * W + r.ix)
                                  : __ldg(hz_v + s_hoff[r.L] + (r.iy >> r.L) * s_hw[r.L] + (r.ix >> r.L));
-    if (zhi < hzv) {
-      if (!(se < 1.0f)) return SSGI_HIT_MISS;
+    if (kmin * hzv > 1.0f) {
+      if (!(se < 1.0f)) return SSGI_HIT_MISS;  // the cell holds the end of the segment
       step_out(r, sx, sy);
-      r.za = zb;
+      r.ka = kb;
       if (r.L + 1 < levels) ++r.L;
     } else if (r.L > 0) {
       --r.L;
-    } else if (zlo <= hzv + A.thickness) {
+    } else if (kmax * (hzv + thick) >= 1.0f) {
       return r.iy * W + r.ix;
     } else {
       if (!(se < 1.0f)) return SSGI_HIT_MISS;
       step_out(r, sx, sy);
-      r.za = zb;
+      r.ka = kb;
     }
   }
 }

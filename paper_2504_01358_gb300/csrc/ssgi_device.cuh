@@ -159,31 +159,22 @@ struct DirAngles {
 
 __device__ __forceinline__ DirAngles dir_angles(float3 d) {
   DirAngles r;
+  // azimuth: pick the octant-reduced (numerator, denominator) pair with selects, one atan2f
   const float X = -d.z, Y = d.x;
-  if (fabsf(Y) <= X) {
-    r.bx = 0.5f;
-    r.ax = atan2f(Y, X);
-  } else if (Y > fabsf(X)) {
-    r.bx = 0.75f;
-    r.ax = atan2f(-X, Y);
-  } else if (-X >= fabsf(Y)) {
-    r.bx = 1.0f;
-    r.ax = atan2f(-Y, -X);
-  } else {
-    r.bx = 0.25f;
-    r.ax = atan2f(X, -Y);
-  }
+  const float aX = fabsf(X), aY = fabsf(Y);
+  const bool xa = aY <= X, xb = Y > aX, xc = -X >= aY;
+  const float num = xa ? Y : (xb ? -X : (xc ? -Y : X));
+  const float den = xa ? X : (xb ? Y : (xc ? -X : -Y));
+  r.bx = xa ? 0.5f : (xb ? 0.75f : (xc ? 1.0f : 0.25f));
+  r.ax = atan2f(num, den);
+  // polar angle from +y, likewise
   const float q = sqrtf(d.x * d.x + d.z * d.z);
-  if (d.y >= q) {
-    r.by = 0.0f;
-    r.ay = atan2f(q, d.y);
-  } else if (-d.y >= q) {
-    r.by = 1.0f;
-    r.ay = -atan2f(q, -d.y);
-  } else {
-    r.by = 0.5f;
-    r.ay = -atan2f(d.y, q);
-  }
+  const bool ya = d.y >= q, yb = -d.y >= q;
+  const float ny = ya ? q : (yb ? q : d.y);
+  const float dy = ya ? d.y : (yb ? -d.y : q);
+  const float sg = (ya ? 1.0f : -1.0f);
+  r.by = ya ? 0.0f : (yb ? 1.0f : 0.5f);
+  r.ay = sg * atan2f(ny, dy);
   return r;
 }
 
