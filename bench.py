@@ -42,6 +42,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-rate", type=float, default=400.0)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
@@ -210,6 +214,156 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------------------------
+# serving (Poisson request stream, mixed resolutions and sample counts)
+# ----------------------------------------------------------------------------------------------
+SERVE_RES = [(360, 640), (720, 1280), (900, 1600), (1080, 1920)]
+SERVE_SPP = [4, 8, 16, 32]
+
+
+def serving_workload(n_requests: int, rate: float, seed: int = 5):
+    """Request list of the serving configuration: Poisson arrivals at `rate`/s, resolution and
+    spp uniform over the four choices, seeded scenes (config-2 generator) and 128x256
+    log-normal environments drawn from pools of 4 scenes per resolution and 32 maps."""
+    import numpy as np
+    import ssgi_inputs as si
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
+    res = rng.integers(0, len(SERVE_RES), size=n_requests)
+    spp = rng.choice(SERVE_SPP, size=n_requests)
+    scenes = {}
+    for r, (H, W) in enumerate(SERVE_RES):
+        for k in range(4):
+            scenes[(r, k)] = si.single_view(f"serve-{W}x{H}-{k}", 100 + 10 * r + k, H, W, 40, 8.0, 2, (128, 256),
+                                            si.TraceParams(spp=4, max_steps=64))
+    envs = [si.lognormal_env(5000 + j, 128, 256) for j in range(32)]
+    reqs = [dict(arrival=float(arrivals[i]), scene=scenes[(int(res[i]), i % 4)], env=envs[i % 32], spp=int(spp[i]),
+                 seed=i, res=int(res[i])) for i in range(n_requests)]
+    return reqs
+
+
+def run_serving(n_requests: int, rate: float, slots: int, budget_gb: float):
+    import numpy as np
+    import torch
+
+    import paper_2504_01358_gb300 as S
+    from paper_2504_01358_gb300 import _native as N
+    from paper_2504_01358_gb300.serve import Server
+
+    reqs = serving_workload(n_requests, rate)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    host = {}
+    for rq in reqs:
+        wl = rq["scene"]
+        if id(wl) not in host:
+            host[id(wl)] = {k: pin(getattr(wl, k)) for k in ("depth", "normal", "albedo", "rough", "metal")}
+    envs = {}
+    for rq in reqs:
+        if id(rq["env"]) not in envs:
+            envs[id(rq["env"])] = pin(rq["env"])
+    ring = 64
+    outs = {r: [torch.empty((1, H, W, 3)).pin_memory() for _ in range(ring)] for r, (H, W) in enumerate(SERVE_RES)}
+
+    def params(rq):
+        return S.TraceParams(spp=rq["spp"], max_steps=64, hiz_levels=8, thickness=0.05, max_distance=100.0,
+                             seed=rq["seed"], flags=0)
+
+    rays = sum(rq["spp"] * rq["scene"].depth.size for rq in reqs)
+
+    # ---- served: continuous batching --------------------------------------------------------
+    srv = Server(int(budget_gb * (1 << 30)), max_slots=slots, queue_capacity=n_requests + 16)
+    # warm up every resolution once
+    for r in range(len(SERVE_RES)):
+        rq = next(q for q in reqs if q["res"] == r)
+        h = host[id(rq["scene"])]
+        rc, t = srv.submit(outs[r][0], envs[id(rq["env"])], params(rq), depth=h["depth"], normal=h["normal"],
+                           albedo=h["albedo"], rough=h["rough"], metal=h["metal"], cams=rq["scene"].cams)
+        srv.wait(t, 60000)
+    tickets = []
+    t0 = time.perf_counter()
+    for i, rq in enumerate(reqs):
+        while time.perf_counter() - t0 < rq["arrival"]:
+            pass
+        h = host[id(rq["scene"])]
+        t_sub = time.perf_counter() - t0
+        rc, t = srv.submit(outs[rq["res"]][i % ring], envs[id(rq["env"])], params(rq), depth=h["depth"],
+                           normal=h["normal"], albedo=h["albedo"], rough=h["rough"], metal=h["metal"],
+                           cams=rq["scene"].cams)
+        if rc != N.OK:
+            raise RuntimeError(f"submit failed: {N.STATUS.get(rc, rc)}")
+        tickets.append((t, t_sub))
+    lat = []
+    for (t, t_sub), rq in zip(tickets, reqs):
+        rc, ms = srv.wait(t, 600000)
+        if rc != N.OK:
+            raise RuntimeError(f"request failed: {N.STATUS.get(rc, rc)}")
+        lat.append(t_sub - rq["arrival"] + ms / 1e3)
+    served_span = max(rq["arrival"] + l for rq, l in zip(reqs, lat)) - reqs[0]["arrival"]
+    st = srv.stats()
+    srv.close()
+
+    # ---- plain: one request at a time, synchronous, preallocated buffers --------------------
+    Hm, Wm = max(SERVE_RES)
+    f = lambda *sh: torch.empty(sh, device="cuda")  # noqa: E731
+    g = S.GBuffer(f(1, Hm, Wm), f(1, Hm, Wm, 3), f(1, Hm, Wm, 3), f(1, Hm, Wm), f(1, Hm, Wm))
+    env_d = f(128, 256, 3)
+    em = S.EnvMap(f(S.ssgi_env_mip_floats(128, 256)), 128, 256)
+    hiz = f(S.ssgi_hiz_floats((1, Hm, Wm), 8))
+    c_d, c1, fin = f(1, Hm, Wm, 3), f(1, Hm, Wm, 3), f(1, Hm, Wm, 3)
+    lut = S.ssgi_build_brdf_lut()
+    stream = torch.cuda.current_stream()
+
+    def plain_one(rq, out):
+        wl = rq["scene"]
+        H, W = wl.depth.shape[1:]
+        n = H * W
+        h = host[id(wl)]
+        gv = S.GBuffer(g.depth.view(-1)[:n].view(1, H, W), g.normal.view(-1)[:3 * n].view(1, H, W, 3),
+                       g.albedo.view(-1)[:3 * n].view(1, H, W, 3), g.rough.view(-1)[:n].view(1, H, W),
+                       g.metal.view(-1)[:n].view(1, H, W))
+        for k in ("depth", "normal", "albedo", "rough", "metal"):
+            getattr(gv, k).copy_(h[k], non_blocking=True)
+        env_d.copy_(envs[id(rq["env"])], non_blocking=True)
+        S.ssgi_build_env_mips(env_d, out=em.mips)
+        hz = hiz[: S.ssgi_hiz_floats((1, H, W), 8)]
+        S.ssgi_build_hiz(gv.depth, 8, out=hz)
+        cd = c_d.view(-1)[:3 * n].view(1, H, W, 3)
+        cc = c1.view(-1)[:3 * n].view(1, H, W, 3)
+        ff = fin.view(-1)[:3 * n].view(1, H, W, 3)
+        S.ssgi_shade_direct(gv, wl.cams, em, lut, c_d=cd, c1=cc)
+        S.ssgi_trace_indirect(gv, wl.cams, hz, cc, cd, em, params(rq), final=ff)
+        out.copy_(ff, non_blocking=True)
+        stream.synchronize()
+
+    for r in range(len(SERVE_RES)):
+        rq = next(q for q in reqs if q["res"] == r)
+        plain_one(rq, outs[r][0])
+    plat = []
+    t0 = time.perf_counter()
+    for i, rq in enumerate(reqs):
+        while time.perf_counter() - t0 < rq["arrival"]:
+            pass
+        plain_one(rq, outs[rq["res"]][i % ring])
+        plat.append(time.perf_counter() - t0 - rq["arrival"])
+    plain_span = max(rq["arrival"] + l for rq, l in zip(reqs, plat)) - reqs[0]["arrival"]
+
+    def pct(a, q):
+        import numpy as np
+        return float(np.percentile(np.asarray(a) * 1e3, q))
+
+    return {"requests": n_requests, "arrival_rate_per_s": rate, "slots": slots, "hbm_budget_gb": budget_gb,
+            "offered_rays_per_s": rays / reqs[-1]["arrival"],
+            "served": {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "mean_ms": 1e3 * sum(lat) / len(lat),
+                       "throughput_req_per_s": n_requests / served_span, "rays_per_s": rays / served_span,
+                       "arena_peak_gb": st["arena_bytes_peak"] / 2 ** 30},
+            "plain": {"p50_ms": pct(plat, 50), "p99_ms": pct(plat, 99), "mean_ms": 1e3 * sum(plat) / len(plat),
+                      "throughput_req_per_s": n_requests / plain_span, "rays_per_s": rays / plain_span},
+            "p99_plain_over_served": pct(plat, 99) / max(pct(lat, 99), 1e-9),
+            "workload": "Poisson arrivals, resolution uniform over 640x360/1280x720/1600x900/1920x1080, spp uniform "
+                        "over 4/8/16/32, scenes from the config-2 generator (pool of 4 per resolution), 128x256 "
+                        "log-normal env maps (pool of 32), 64 steps, 8 levels; latency = arrival to result on host"}
+
+
+# ----------------------------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------------------------
 def run_ours(args):
@@ -270,6 +424,7 @@ def run_ours(args):
         ms = float(t.item())
     value = world * rays / (ms / 1e3)
     trace_ms = stage_ms["trace"]
+    launches = pipe.kernels_per_step() * args.steps
 
     # march iterations of one trace launch (counted by the kernel itself, untimed)
     counter = torch.zeros(1, device="cuda", dtype=torch.int64)
@@ -330,6 +485,11 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl)
+    serving = None
+    if rank == 0 and not args.no_serving:
+        del pipe
+        torch.cuda.empty_cache()
+        serving = run_serving(args.serve_requests, args.serve_rate, args.serve_slots, 100.0)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -339,7 +499,7 @@ def run_ours(args):
                 "fwd_bwd_ms": ms, "trace_rays_per_s": rays / (trace_ms / 1e3),
                 "stage_ms": stage_ms, "wall_s": t_wall,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": pipe.kernels_per_step() * args.steps, "clocks": clocks}
+                "gpu_launches": launches, "clocks": clocks, "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

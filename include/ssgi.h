@@ -13,9 +13,9 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  * Memory.  Every array pointer is a DEVICE pointer owned by the caller unless the argument
- *   says "host".  The library never frees or retains caller memory; it allocates nothing
- *   except inside ssgi_serve_create.  All arrays are dense, C-contiguous FP32 (int32 for
- *   hit indices), 4-byte aligned.
+ *   says "host".  The library never frees or retains caller memory; the only device
+ *   memory it allocates is a serving arena, inside ssgi_serve_create.  All arrays are
+ *   dense, C-contiguous FP32 (int32 for hit indices), 4-byte aligned.
  * Streams.  Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL = the legacy
  *   default stream).  A call returns after argument validation and launch; device-side
  *   faults surface as SSGI_ERR_CUDA from this or a later call.
@@ -201,6 +201,78 @@ ssgi_status ssgi_backward(const float *g_final, const ssgi_gbuffer *g, const ssg
                           const ssgi_envmap *env, const float *lut, int32_t lut_n, const int32_t *hit_idx,
                           const ssgi_trace_params *p, float *g_albedo, float *g_rough, float *g_metal,
                           float *g_normal, float *g_env, void *workspace, size_t ws_bytes, ssgi_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Serving: continuous batching of render requests (real-time relighting / material editing,  */
+/* Sec. 4 "Editing"; the per-request work is steps mips -> Hi-Z -> direct -> trace above).     */
+/*                                                                                            */
+/* A server owns one device arena of hbm_budget_bytes (allocated by ssgi_serve_create; the    */
+/* only allocation the library makes) and max_slots CUDA streams.  An engine thread admits    */
+/* queued requests in arrival order whenever a slot is free and the arena has room for the   */
+/* request's buffers, enqueues its copies and kernels on the slot's stream, and retires it    */
+/* when its completion event fires; admitted requests of different slots run concurrently on  */
+/* the device.  Scenes (G-buffer + camera + Hi-Z pyramid) can be made resident once and then  */
+/* re-rendered by many requests with new environment maps or materials edits applied on the  */
+/* host.  All waits are bounded; nothing on the device spins.                                 */
+/* ---------------------------------------------------------------------------------------- */
+typedef struct ssgi_server ssgi_server;
+
+typedef struct {
+  size_t hbm_budget_bytes; /* device arena size; requests and resident scenes are carved from it */
+  int32_t max_slots;       /* requests on the GPU at once (1..64); each slot has its own stream */
+  int32_t queue_capacity;  /* requests submitted but not yet admitted (>= 1) */
+  int32_t lut_n, lut_samples; /* BRDF table built at create (0 = 64, 4096) */
+} ssgi_serve_config;
+
+/* One render request.  Host arrays must stay valid until the request completes; pinned host
+ * memory lets its copies overlap other requests' kernels.  scene >= 0 renders a resident scene
+ * (depth..metal, cams and d are then ignored); scene < 0 uploads the request's own G-buffer. */
+typedef struct {
+  int64_t scene;
+  ssgi_dims d;                                      /* views, height, width */
+  const float *depth, *normal, *albedo, *rough, *metal; /* host, layouts as ssgi_gbuffer */
+  const ssgi_camera *cams;                          /* host, d.views cameras */
+  const float *env;                                 /* host [env_h][env_w][3] */
+  int32_t env_h, env_w;
+  ssgi_trace_params params;
+  float *final_out;                                 /* host [V,H,W,3], written on completion */
+} ssgi_request;
+
+typedef struct {
+  uint64_t submitted, admitted, completed, cancelled, rejected;
+  int32_t queued, in_flight, resident_scenes, pad_;
+  size_t arena_bytes_in_use, arena_bytes_peak;
+} ssgi_serve_stats;
+
+/* Create a server: allocates the arena and builds the BRDF table on the current device.
+ * SSGI_ERR_OOM if the arena cannot be allocated. */
+ssgi_status ssgi_serve_create(const ssgi_serve_config *cfg, ssgi_server **out);
+/* Upload a G-buffer (host arrays) and build its pyramid once; *scene receives its id.
+ * Synchronous.  SSGI_ERR_BUDGET if the arena has no room for it now. */
+ssgi_status ssgi_serve_scene_add(ssgi_server *s, ssgi_dims d, const float *depth, const float *normal,
+                                 const float *albedo, const float *rough, const float *metal,
+                                 const ssgi_camera *cams, int32_t hiz_levels, int64_t *scene);
+/* Release a resident scene; SSGI_ERR_NOT_READY while requests that use it are queued or running. */
+ssgi_status ssgi_serve_scene_remove(ssgi_server *s, int64_t scene);
+/* Queue a request; *ticket identifies it.  SSGI_ERR_QUEUE_FULL when queue_capacity requests
+ * wait; SSGI_ERR_BUDGET when the request alone is larger than the whole arena;
+ * SSGI_ERR_INVALID_ARG for malformed requests (checked before anything is queued). */
+ssgi_status ssgi_serve_submit(ssgi_server *s, const ssgi_request *req, uint64_t *ticket);
+/* SSGI_OK once the request finished (final_out written; *latency_ms = submit to completion,
+ * optional), SSGI_ERR_NOT_READY before, SSGI_ERR_CANCELLED if it was cancelled,
+ * SSGI_ERR_CUDA if its work failed, SSGI_ERR_INVALID_ARG for an unknown or already
+ * collected ticket.  A finished ticket is forgotten once OK/CANCELLED/CUDA is returned. */
+ssgi_status ssgi_serve_poll(ssgi_server *s, uint64_t ticket, double *latency_ms);
+/* Like poll, blocking up to timeout_ms; SSGI_ERR_TIMEOUT if the request is still unfinished. */
+ssgi_status ssgi_serve_wait(ssgi_server *s, uint64_t ticket, uint32_t timeout_ms, double *latency_ms);
+/* Cancel a request that has not been admitted yet; SSGI_ERR_NOT_READY if it is already running. */
+ssgi_status ssgi_serve_cancel(ssgi_server *s, uint64_t ticket);
+ssgi_status ssgi_serve_stats_get(ssgi_server *s, ssgi_serve_stats *out);
+/* Stop: cancel queued requests, wait (bounded, timeout_ms) for running ones, free everything.
+ * SSGI_ERR_TIMEOUT if running work did not finish in time (resources are then kept, not freed). */
+ssgi_status ssgi_serve_destroy(ssgi_server *s, uint32_t timeout_ms);
+/* Device bytes a request of these sizes needs in the arena (0 if the sizes are invalid). */
+size_t ssgi_serve_request_bytes(ssgi_dims d, int32_t env_h, int32_t env_w, int32_t hiz_levels, int32_t resident);
 
 /* ---------------------------------------------------------------------------------------- */
 /* Allocation-free backward (no counterpart in the paper; an interface convenience)          */

@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(_PKG, "libssgi.so")
 
 SSGI_MAX_VIEWS = 32
 BACKWARD_NOALLOC_MAX_BYTES = 32 << 20
+OK, INVALID_ARG, UNSUPPORTED, CUDA_ERR, OOM, BUDGET, QUEUE_FULL, TIMEOUT, NOT_READY, CANCELLED = range(10)
 HIT_MISS, HIT_INVALID, HIT_BACKGROUND = -1, -2, -3
 DIFFUSE_INDIRECT = 1
 BRUTE_FORCE = 2
@@ -52,6 +53,25 @@ class TraceParams(C.Structure):
                 ("max_distance", C.c_float), ("seed", C.c_uint64), ("flags", C.c_uint32)]
 
 
+class ServeConfig(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_slots", C.c_int32), ("queue_capacity", C.c_int32),
+                ("lut_n", C.c_int32), ("lut_samples", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("scene", C.c_int64), ("d", Dims), ("depth", C.c_void_p), ("normal", C.c_void_p),
+                ("albedo", C.c_void_p), ("rough", C.c_void_p), ("metal", C.c_void_p), ("cams", C.c_void_p),
+                ("env", C.c_void_p), ("env_h", C.c_int32), ("env_w", C.c_int32), ("params", TraceParams),
+                ("final_out", C.c_void_p)]
+
+
+class ServeStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("admitted", C.c_uint64), ("completed", C.c_uint64),
+                ("cancelled", C.c_uint64), ("rejected", C.c_uint64), ("queued", C.c_int32),
+                ("in_flight", C.c_int32), ("resident_scenes", C.c_int32), ("pad_", C.c_int32),
+                ("arena_bytes_in_use", C.c_size_t), ("arena_bytes_peak", C.c_size_t)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -76,6 +96,16 @@ _SIGS = {
                                 C.POINTER(TraceParams), VP, VP, VP, VP, VP, VP, SZ, VP]),
     "ssgi_backward_noalloc": (C.c_int, [VP, C.POINTER(GBuffer), C.POINTER(Camera), VP, C.POINTER(EnvMap), VP, I32,
                                         VP, C.POINTER(TraceParams), VP, VP, VP, VP, VP, VP]),
+    "ssgi_serve_create": (C.c_int, [C.POINTER(ServeConfig), C.POINTER(VP)]),
+    "ssgi_serve_scene_add": (C.c_int, [VP, Dims, VP, VP, VP, VP, VP, VP, I32, C.POINTER(I64)]),
+    "ssgi_serve_scene_remove": (C.c_int, [VP, I64]),
+    "ssgi_serve_submit": (C.c_int, [VP, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+    "ssgi_serve_poll": (C.c_int, [VP, C.c_uint64, C.POINTER(C.c_double)]),
+    "ssgi_serve_wait": (C.c_int, [VP, C.c_uint64, C.c_uint32, C.POINTER(C.c_double)]),
+    "ssgi_serve_cancel": (C.c_int, [VP, C.c_uint64]),
+    "ssgi_serve_stats_get": (C.c_int, [VP, C.POINTER(ServeStats)]),
+    "ssgi_serve_destroy": (C.c_int, [VP, C.c_uint32]),
+    "ssgi_serve_request_bytes": (SZ, [Dims, I32, I32, I32, I32]),
 }
 
 # every symbol include/ssgi.h declares (checked by the CPU tests)

@@ -78,3 +78,21 @@ def test_invalid_arguments_fail_before_any_launch(N):
     assert L.ssgi_backward(fake, C.byref(g), cam, fake, C.byref(env), fake, 64, fake, C.byref(p), fake, fake, fake,
                            fake, fake, fake, 16, None) == 1
     assert L.ssgi_l2_loss(fake, fake, 0, fake, None, None) == 1
+
+
+def test_serving_host_side_checks(N):
+    L = N.lib()
+    d = N.Dims(1, 90, 160)
+    full = L.ssgi_serve_request_bytes(d, 16, 32, 8, 0)
+    resident = L.ssgi_serve_request_bytes(d, 16, 32, 8, 1)
+    px = 90 * 160
+    assert resident >= px * 36 and full >= resident + px * 36 + 4 * O.hiz_floats_per_view(90, 160, 8)
+    assert L.ssgi_serve_request_bytes(d, 3, 8, 8, 0) == 0
+    cfg = N.ServeConfig(16, 4, 8, 0, 0)  # budget below the minimum
+    h = C.c_void_p()
+    assert L.ssgi_serve_create(C.byref(cfg), C.byref(h)) == 1
+    cfg = N.ServeConfig(1 << 30, 0, 8, 0, 0)  # no slots
+    assert L.ssgi_serve_create(C.byref(cfg), C.byref(h)) == 1
+    assert L.ssgi_serve_submit(None, None, None) == 1
+    assert L.ssgi_serve_poll(None, 1, None) == 1
+    assert L.ssgi_serve_destroy(None, 0) == 1
