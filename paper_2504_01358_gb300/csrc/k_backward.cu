@@ -130,7 +130,7 @@ __device__ __forceinline__ float3 env_lookup_adj(const float* __restrict__ mips,
 // ------------------------------------------------------------------------------------------
 // K4a: Monte-Carlo adjoint, one thread per receiver pixel.
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_bwd_mc(BwdArgs A) {
+__global__ void __launch_bounds__(256, 4) k_bwd_mc(BwdArgs A) {
   const long long HW = (long long)A.vs.H * A.vs.W;
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= HW * A.vs.V) return;

@@ -151,7 +151,7 @@ __device__ __forceinline__ int march(const TraceArgs& A, const DevCam& c, const 
 // One thread per pixel, looping over its samples; a warp covers an 8 x 4 tile so that its
 // rays start close together and touch the same pyramid cells.
 template <bool kCid>
-__global__ void __launch_bounds__(kTileW * kTileH, 6) k_trace(TraceArgs A) {
+__global__ void __launch_bounds__(kTileW * kTileH, 8) k_trace(TraceArgs A) {
   __shared__ int s_hoff[SSGI_MAX_HIZ_LEVELS], s_hw[SSGI_MAX_HIZ_LEVELS];
   if (threadIdx.x < SSGI_MAX_HIZ_LEVELS) {
     s_hoff[threadIdx.x] = A.hz.off[threadIdx.x];
