@@ -203,6 +203,28 @@ ssgi_status ssgi_backward(const float *g_final, const ssgi_gbuffer *g, const ssg
                           float *g_normal, float *g_env, void *workspace, size_t ws_bytes, ssgi_stream_t stream);
 
 /* ---------------------------------------------------------------------------------------- */
+/* Fused inverse-rendering step: every stage above for all views of a frame in ONE persistent  */
+/* cooperative launch (env mips, Hi-Z, direct shading, trace with stored hits, L2 loss against */
+/* `target`, backward).  Same per-item code as the separate calls, so final and hit_idx equal  */
+/* theirs bit for bit and the gradients agree up to the order of atomic additions.            */
+/* ---------------------------------------------------------------------------------------- */
+/* workspace bytes of ssgi_step_fused (mips, pyramid, c_d, c1, g_final and the backward scratch) */
+size_t ssgi_step_fused_workspace_bytes(ssgi_dims d, int32_t env_h, int32_t env_w, int32_t hiz_levels);
+/* env: device base level [env_h][env_w][3]; target: device [V,H,W,3]; outputs: final_out
+ * [V,H,W,3], hit_idx [V,H,W,spp], loss (one device float), gradients as ssgi_backward.
+ * workspace: 256-byte aligned, >= ssgi_step_fused_workspace_bytes.  SSGI_ERR_UNSUPPORTED
+ * without cooperative-launch support.  The stages are separated by a grid barrier whose wait is
+ * bounded; if a block ever gives up waiting every block stops and ssgi_step_fused_check
+ * reports it (the outputs are then incomplete). */
+ssgi_status ssgi_step_fused(const ssgi_gbuffer *g, const ssgi_camera *cams, const float *env, int32_t env_h,
+                            int32_t env_w, const float *lut, int32_t lut_n, const float *target,
+                            const ssgi_trace_params *p, float *final_out, int32_t *hit_idx, float *loss,
+                            float *g_albedo, float *g_rough, float *g_metal, float *g_normal, float *g_env,
+                            void *workspace, size_t ws_bytes, ssgi_stream_t stream);
+/* Synchronous: *failed = 1 if the last fused step on this workspace stopped at a barrier. */
+ssgi_status ssgi_step_fused_check(const void *workspace, int32_t *failed);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Serving: continuous batching of render requests (real-time relighting / material editing,  */
 /* Sec. 4 "Editing"; the per-request work is steps mips -> Hi-Z -> direct -> trace above).     */
 /*                                                                                            */

@@ -1,7 +1,7 @@
 // k_prep.cu -- per-frame and per-environment precomputation: the BRDF-integral table
 // (Appendix C), the environment mip chain (Sec. 3.2, SampleEnvMap) and the hierarchical-Z
-// pyramid used by the screen-space march (Sec. 3.3).
-#include "ssgi_device.cuh"
+// pyramid used by the screen-space march (Sec. 3.3).  Stage bodies live in ssgi_ops.cuh.
+#include "ssgi_ops.cuh"
 
 namespace ssgi {
 
@@ -43,76 +43,21 @@ __global__ void __launch_bounds__(256) k_brdf_lut(int N, int M, float* __restric
   }
 }
 
-// ------------------------------------------------------------------------------------------
-// Environment mips: level l texel = mean of its 2x2 children at level l-1.
-// ------------------------------------------------------------------------------------------
 __global__ void k_env_down(const float* __restrict__ src, int hs, int ws, float* __restrict__ dst) {
-  const int hd = hs >> 1, wd = ws >> 1;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= hd * wd * 3) return;
-  const int c = t % 3, j = (t / 3) % wd, i = t / (3 * wd);
-  const float a = src[((2 * i) * ws + 2 * j) * 3 + c], b = src[((2 * i) * ws + 2 * j + 1) * 3 + c];
-  const float d = src[((2 * i + 1) * ws + 2 * j) * 3 + c], e = src[((2 * i + 1) * ws + 2 * j + 1) * 3 + c];
-  dst[t] = 0.25f * (((a + b) + d) + e);
+  if (t >= (hs >> 1) * (ws >> 1) * 3) return;
+  env_down_item(src, hs, ws, dst, t);
 }
-
-// ------------------------------------------------------------------------------------------
-// Hi-Z: one launch reduces a 32x32 depth tile per block through levels 1..5 in shared
-// memory (min is exact, so any grouping gives the same bits); a second launch per remaining
-// level continues from level 5.
-// ------------------------------------------------------------------------------------------
-constexpr int kHizTile = 32;  // level-0 pixels per block side; covers levels 1..5
 
 __global__ void __launch_bounds__(256) k_hiz_tile(const float* __restrict__ depth, int H, int W, HizInfo hz,
                                                   float* __restrict__ hiz) {
-  __shared__ float s[kHizTile][kHizTile + 1];
-  const int view = blockIdx.z;
-  const int bx = blockIdx.x * kHizTile, by = blockIdx.y * kHizTile;
-  const float* d0 = depth + (size_t)view * H * W;
-  float* out = hiz + (size_t)view * hz.per_view;
-  for (int k = threadIdx.x; k < kHizTile * kHizTile; k += blockDim.x) {
-    const int ty = k / kHizTile, tx = k % kHizTile;
-    const int y = by + ty, x = bx + tx;
-    s[ty][tx] = (y < H && x < W) ? __ldg(d0 + (size_t)y * W + x) : INFINITY;
-  }
-  __syncthreads();
-  int n = kHizTile;
-  const int top = min(hz.levels - 1, 5);
-  for (int l = 1; l <= top; ++l) {
-    n >>= 1;
-    float m = INFINITY;
-    int ty = 0, tx = 0;
-    const bool act = threadIdx.x < n * n;
-    if (act) {
-      ty = threadIdx.x / n;
-      tx = threadIdx.x % n;
-      m = fminf(fminf(s[2 * ty][2 * tx], s[2 * ty][2 * tx + 1]), fminf(s[2 * ty + 1][2 * tx], s[2 * ty + 1][2 * tx + 1]));
-    }
-    __syncthreads();
-    if (act) {
-      s[ty][tx] = m;
-      const int gy = (by >> l) + ty, gx = (bx >> l) + tx;
-      if (gy < hz.h[l] && gx < hz.w[l]) out[hz.off[l] + gy * hz.w[l] + gx] = m;
-    }
-    __syncthreads();
-  }
+  hiz_tile_block(depth, H, W, hz, hiz, blockIdx.z, blockIdx.x, blockIdx.y);
 }
 
 __global__ void k_hiz_level(int V, HizInfo hz, int l, float* __restrict__ hiz) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int w = hz.w[l], h = hz.h[l];
-  if (t >= V * w * h) return;
-  const int view = t / (w * h), rem = t % (w * h);
-  const int i = rem / w, j = rem % w;
-  const float* src = hiz + (size_t)view * hz.per_view + hz.off[l - 1];
-  const int ws = hz.w[l - 1], hs = hz.h[l - 1];
-  float m = src[(2 * i) * ws + 2 * j];
-  if (2 * j + 1 < ws) m = fminf(m, src[(2 * i) * ws + 2 * j + 1]);
-  if (2 * i + 1 < hs) {
-    m = fminf(m, src[(2 * i + 1) * ws + 2 * j]);
-    if (2 * j + 1 < ws) m = fminf(m, src[(2 * i + 1) * ws + 2 * j + 1]);
-  }
-  hiz[(size_t)view * hz.per_view + hz.off[l] + rem] = m;
+  if (t >= V * hz.w[l] * hz.h[l]) return;
+  hiz_level_item(hz, l, hiz, t);
 }
 
 }  // namespace ssgi

@@ -1,0 +1,587 @@
+// ssgi_ops.cuh -- the per-item device code of every SSGI stage, shared by the stand-alone
+// kernels (one launch per stage) and the fused persistent step (all stages in one launch).
+//
+// FrameArgs describes one frame's buffers; each stage reads the fields it needs.
+#pragma once
+
+#include <limits.h>
+
+#include "ssgi_device.cuh"
+
+namespace ssgi {
+
+struct FrameArgs {
+  Views vs;
+  EnvInfo e;
+  HizInfo hz;
+  const float* __restrict__ depth;
+  const float* __restrict__ normal;
+  const float* __restrict__ albedo;
+  const float* __restrict__ rough;
+  const float* __restrict__ metal;
+  const float* __restrict__ mips;  // packed mip chain (built before the stages that read it)
+  const float* __restrict__ lut;
+  const float* __restrict__ hiz;
+  const float* __restrict__ target;
+  int lut_n;
+  float* c_d;
+  float* c_s;
+  float* c1;
+  float* c_s_mc;
+  float* c_id;
+  float* final_out;
+  int32_t* hit_idx;
+  unsigned long long* step_count;
+  float* g_final;
+  float* g_albedo;
+  float* g_rough;
+  float* g_metal;
+  float* g_normal;
+  float* g_c1;    // backward workspace [V,H,W,3]
+  float* g_mips;  // backward workspace, packed like the mips
+  int spp, max_steps, levels;
+  float thickness, max_distance;
+  uint64_t seed;
+  uint32_t flags;
+};
+
+// ==========================================================================================
+// Precomputation (Appendix C table, Sec. 3.2 mips, Sec. 3.3 pyramid)
+// ==========================================================================================
+__device__ __forceinline__ void env_down_item(const float* __restrict__ src, int hs, int ws, float* __restrict__ dst,
+                                              int t) {
+  const int wd = ws >> 1;
+  const int c = t % 3, j = (t / 3) % wd, i = t / (3 * wd);
+  const float a = src[((2 * i) * ws + 2 * j) * 3 + c], b = src[((2 * i) * ws + 2 * j + 1) * 3 + c];
+  const float d = src[((2 * i + 1) * ws + 2 * j) * 3 + c], e = src[((2 * i + 1) * ws + 2 * j + 1) * 3 + c];
+  dst[t] = 0.25f * (((a + b) + d) + e);
+}
+
+
+constexpr int kHizTile = 32;  // level-0 pixels per block side; covers levels 1..5
+
+// Block-level: every thread of the block calls it for the same tile (it synchronises the block);
+// the block has at least 128 threads.
+__device__ __forceinline__ void hiz_tile_block(const float* __restrict__ depth, int H, int W, const HizInfo& hz,
+                                               float* __restrict__ hiz, int view, int tile_x, int tile_y) {
+  __shared__ float s[kHizTile][kHizTile + 1];
+  const int bx = tile_x * kHizTile, by = tile_y * kHizTile;
+  const float* d0 = depth + (size_t)view * H * W;
+  float* out = hiz + (size_t)view * hz.per_view;
+  for (int k = threadIdx.x; k < kHizTile * kHizTile; k += blockDim.x) {
+    const int ty = k / kHizTile, tx = k % kHizTile;
+    const int y = by + ty, x = bx + tx;
+    s[ty][tx] = (y < H && x < W) ? __ldg(d0 + (size_t)y * W + x) : INFINITY;
+  }
+  __syncthreads();
+  int n = kHizTile;
+  const int top = min(hz.levels - 1, 5);
+  // a level has at most 16 x 16 outputs: with >= 128 threads each thread owns at most two
+  constexpr int kPer = (kHizTile / 2) * (kHizTile / 2) / 128;
+  for (int l = 1; l <= top; ++l) {
+    n >>= 1;
+    float m[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int k = threadIdx.x + j * blockDim.x;
+      m[j] = INFINITY;
+      if (k < n * n) {
+        const int ty = k / n, tx = k % n;
+        m[j] = fminf(fminf(s[2 * ty][2 * tx], s[2 * ty][2 * tx + 1]), fminf(s[2 * ty + 1][2 * tx], s[2 * ty + 1][2 * tx + 1]));
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int k = threadIdx.x + j * blockDim.x;
+      if (k < n * n) {
+        const int ty = k / n, tx = k % n;
+        s[ty][tx] = m[j];
+        const int gy = (by >> l) + ty, gx = (bx >> l) + tx;
+        if (gy < hz.h[l] && gx < hz.w[l]) out[hz.off[l] + gy * hz.w[l] + gx] = m[j];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ void hiz_level_item(const HizInfo& hz, int l, float* __restrict__ hiz, int t) {
+  const int w = hz.w[l], h = hz.h[l];
+  const int view = t / (w * h), rem = t % (w * h);
+  const int i = rem / w, j = rem % w;
+  const float* src = hiz + (size_t)view * hz.per_view + hz.off[l - 1];
+  const int ws = hz.w[l - 1], hs = hz.h[l - 1];
+  float m = src[(2 * i) * ws + 2 * j];
+  if (2 * j + 1 < ws) m = fminf(m, src[(2 * i) * ws + 2 * j + 1]);
+  if (2 * i + 1 < hs) {
+    m = fminf(m, src[(2 * i + 1) * ws + 2 * j]);
+    if (2 * j + 1 < ws) m = fminf(m, src[(2 * i + 1) * ws + 2 * j + 1]);
+  }
+  hiz[(size_t)view * hz.per_view + hz.off[l] + rem] = m;
+}
+
+// ==========================================================================================
+// Direct shading (Sec. 3.2)
+// ==========================================================================================
+// Direct shading of pixel p (flat index over [V,H,W]).
+__device__ __forceinline__ void shade_pixel(const FrameArgs& A, long long p) {
+  const Views& vs = A.vs;
+  const EnvInfo& e = A.e;
+  const long long HW = (long long)vs.H * vs.W;
+  const int view = (int)(p / HW);
+  const int rem = (int)(p - (long long)view * HW);
+  const int y = rem / vs.W, x = rem - (rem / vs.W) * vs.W;
+  const DevCam& cam = vs.cam[view];
+  const float3 d = pix_dir_world(cam, x, y);
+  const float z = __ldg(A.depth + p);
+  float3 od = f3(0.f, 0.f, 0.f), os = f3(0.f, 0.f, 0.f), o1;
+  if (is_background(z)) {
+    o1 = env_lookup0(A.mips, e, d);
+  } else {
+    const float3 v = d * (-1.0f / sqrtf(dot3(d, d)));
+    const float3 n = ld3(A.normal + 3 * p);
+    const float nv = dot3(n, v);
+    const float mu = fminf(fmaxf(nv, 1e-4f), 1.0f);
+    const float3 r = n * (2.0f * nv) - v;
+    const float rho = __ldg(A.rough + p), m = __ldg(A.metal + p);
+    const float lam = log2f(rho + 1.0f) * (float)(e.levels - 1);
+    const LutVal ab = lut_sample(A.lut, A.lut_n, rho, mu);
+    const float3 Er = env_lookup(A.mips, e, r, lam);
+    const float3 En = env_lookup(A.mips, e, n, lam);
+    const float3 a = ld3(A.albedo + 3 * p);
+    const float3 F0 = f3(f0_of(a.x, m), f0_of(a.y, m), f0_of(a.z, m));
+    os = mul3(Er, F0 * ab.A + f3(ab.B, ab.B, ab.B));
+    od = mul3(a * (1.0f - m), En);
+    o1 = od + os;
+  }
+  st3(A.c_d + 3 * p, od);
+  if (A.c_s) st3(A.c_s + 3 * p, os);
+  st3(A.c1 + 3 * p, o1);
+}
+
+
+// ==========================================================================================
+// Trace (Sec. 3.3, Appendix D)
+// ==========================================================================================
+// One ray's march state.  The segment constants give the exit parameter of a cell edge bx as
+// s_x = bx * iDx + ox (iDx = 0, ox = +inf when the segment has no x extent).  Depth is handled
+// as k = 1/z, which is linear in the screen parameter, and the tests are written on k:
+//   z_hi < hz          <=>  k_min * hz > 1
+//   z_lo <= hz + thick <=>  k_max * (hz + thick) >= 1
+// (k > 0 on the clipped segment), so an iteration has no division; ka caches k at the cell
+// entry.
+struct Ray {
+  float P0x, P0y, Dx, Dy, iDx, iDy, ox, oy, k0, dk, ka;
+  int ix, iy, L, sgx, sgy;
+};
+
+// Exit parameters of the level-L cell holding (ix, iy).
+__device__ __forceinline__ void exits(const Ray& r, float& sx, float& sy) {
+  sx = fmaf((float)(((r.ix >> r.L) + r.sgx) << r.L), r.iDx, r.ox);
+  sy = fmaf((float)(((r.iy >> r.L) + r.sgy) << r.L), r.iDy, r.oy);
+}
+
+// Enter the pixel across the exit side of the level-L cell (ties go to x), on the row (column)
+// of the exit point clamped to the cell.
+__device__ __forceinline__ void step_out(Ray& r, float sx, float sy) {
+  const int lo_x = (r.ix >> r.L) << r.L, lo_y = (r.iy >> r.L) << r.L;
+  const int S1 = (1 << r.L) - 1;
+  if (sx <= sy) {
+    const int fy = __float2int_rd(fmaf(sx, r.Dy, r.P0y));
+    r.iy = min(max(fy, lo_y), lo_y + S1);
+    r.ix = r.sgx ? lo_x + S1 + 1 : lo_x - 1;
+  } else {
+    const int fx = __float2int_rd(fmaf(sy, r.Dx, r.P0x));
+    r.ix = min(max(fx, lo_x), lo_x + S1);
+    r.iy = r.sgy ? lo_y + S1 + 1 : lo_y - 1;
+  }
+}
+
+// March from pixel (x, y) at linear depth z0 (k0 = 1/z0) along camera-space direction w.
+// Returns the hit pixel's index within the view, or SSGI_HIT_MISS; `it` gets the iterations.
+__device__ __forceinline__ int march(const FrameArgs& A, const DevCam& c, const float* __restrict__ dep,
+                                     const float* __restrict__ hz_v, const int* __restrict__ s_hoff,
+                                     const int* __restrict__ s_hw, int levels, int max_steps, int x, int y,
+                                     float z0, float k0, float3 w, int& it) {
+  const int H = A.vs.H, W = A.vs.W;
+  it = 0;
+  const float3 o = pix_dir_cam(c, x, y) * z0;
+  const float wz = -w.z;
+  float t_end = A.max_distance;
+  if (wz < 0.0f) t_end = fminf(t_end, (c.znear - z0) / wz);
+  if (!(t_end > 0.0f)) return SSGI_HIT_MISS;
+  const float3 X1 = o + w * t_end;
+  const float z1 = -X1.z;
+  Ray r;
+  r.P0x = (float)x + 0.5f;
+  r.P0y = (float)y + 0.5f;
+  r.Dx = (c.cx + c.f * X1.x / z1) - r.P0x;
+  r.Dy = (c.cy - c.f * X1.y / z1) - r.P0y;
+  r.iDx = r.Dx != 0.0f ? 1.0f / r.Dx : 0.0f;
+  r.iDy = r.Dy != 0.0f ? 1.0f / r.Dy : 0.0f;
+  r.ox = r.Dx != 0.0f ? -r.P0x * r.iDx : INFINITY;
+  r.oy = r.Dy != 0.0f ? -r.P0y * r.iDy : INFINITY;
+  r.sgx = r.Dx > 0.0f ? 1 : 0;
+  r.sgy = r.Dy > 0.0f ? 1 : 0;
+  r.k0 = k0;
+  r.dk = 1.0f / z1 - k0;
+  r.ix = x;
+  r.iy = y;
+  r.L = 0;
+  float sx, sy;
+  exits(r, sx, sy);  // leave the origin pixel untested
+  const float s0 = fminf(sx, sy);
+  if (!(s0 < 1.0f)) return SSGI_HIT_MISS;
+  step_out(r, sx, sy);
+  r.ka = fmaf(s0, r.dk, r.k0);
+  const float thick = A.thickness;
+
+  for (;;) {
+    if ((unsigned)r.ix >= (unsigned)W || (unsigned)r.iy >= (unsigned)H || it >= max_steps) return SSGI_HIT_MISS;
+    ++it;
+    exits(r, sx, sy);
+    const float se = fminf(sx, sy);
+    const float kb = fmaf(fminf(se, 1.0f), r.dk, r.k0);
+    const float kmin = fminf(r.ka, kb), kmax = fmaxf(r.ka, kb);
+    const float hzv = (r.L == 0) ? __ldg(dep + r.iy * W + r.ix)
+                                 : __ldg(hz_v + s_hoff[r.L] + (r.iy >> r.L) * s_hw[r.L] + (r.ix >> r.L));
+    if (kmin * hzv > 1.0f) {
+      if (!(se < 1.0f)) return SSGI_HIT_MISS;  // the cell holds the end of the segment
+      step_out(r, sx, sy);
+      r.ka = kb;
+      if (r.L + 1 < levels) ++r.L;
+    } else if (r.L > 0) {
+      --r.L;
+    } else if (kmax * (hzv + thick) >= 1.0f) {
+      return r.iy * W + r.ix;
+    } else {
+      if (!(se < 1.0f)) return SSGI_HIT_MISS;
+      step_out(r, sx, sy);
+      r.ka = kb;
+    }
+  }
+}
+
+// Trace all samples of pixel (x, y) of `view`: GGX sampling, march, gather, Monte-Carlo sum
+// and composite (one thread per pixel).
+template <bool kCid>
+__device__ __forceinline__ void trace_pixel(const FrameArgs& A, int x, int y, int view,
+                                            const int* __restrict__ s_hoff, const int* __restrict__ s_hw) {
+  const int W = A.vs.W, H = A.vs.H;
+  const long long HW = (long long)H * W;
+  const int rem = y * W + x;
+  const long long p = (long long)view * HW + rem;
+  const int spp = A.spp;
+  const float z0 = __ldg(A.depth + p);
+  if (is_background(z0)) {
+    const float3 v1 = ld3(A.c1 + 3 * p);
+    st3(A.final_out + 3 * p, v1);
+    if (A.c_s_mc) st3(A.c_s_mc + 3 * p, f3(0.f, 0.f, 0.f));
+    if (A.c_id) st3(A.c_id + 3 * p, f3(0.f, 0.f, 0.f));
+    if (A.hit_idx)
+      for (int s = 0; s < spp; ++s) A.hit_idx[p * spp + s] = SSGI_HIT_BACKGROUND;
+    return;
+  }
+  const DevCam& cam = A.vs.cam[view];
+  const bool brute = (A.flags & SSGI_BRUTE_FORCE) != 0;
+  const int levels = brute ? 1 : A.levels;
+  const int max_steps = brute ? INT_MAX : A.max_steps;
+  const float* dep = A.depth + view * HW;
+  const float* hz_v = A.hiz ? A.hiz + (long long)view * A.hz.per_view : nullptr;
+
+  const float3 d = pix_dir_world(cam, x, y);
+  const float3 v = d * (-1.0f / sqrtf(dot3(d, d)));
+  const float3 n = ld3(A.normal + 3 * p);
+  const float nv = dot3(n, v);
+  const float rho = __ldg(A.rough + p), m = __ldg(A.metal + p);
+  const float3 a = ld3(A.albedo + 3 * p);
+  const float3 F0 = f3(f0_of(a.x, m), f0_of(a.y, m), f0_of(a.z, m));
+  const float g1v = ggx_G1(nv, rho);
+  const float k0 = 1.0f / z0;
+  float3 acc = f3(0.f, 0.f, 0.f), accd = f3(0.f, 0.f, 0.f);
+  unsigned long long steps = 0;
+
+  for (int s = 0; s < spp; ++s) {
+    const float2 xi = sample_uniforms(A.seed, view, (uint32_t)rem, (uint32_t)s);
+    const Sample sm = make_sample(n, v, nv, rho, xi);
+    int q = SSGI_HIT_INVALID;
+    if (sm.valid) {
+      int it;
+      q = march(A, cam, dep, hz_v, s_hoff, s_hw, levels, max_steps, x, y, z0, k0, world_to_cam(cam, sm.w), it);
+      steps += (unsigned long long)it;
+      const float3 Li = q >= 0 ? ld3(A.c1 + 3 * (view * HW + q)) : env_lookup0(A.mips, A.e, sm.w);
+      const float K = ggx_G1(sm.nw, rho) * g1v * sm.vh / (nv * sm.nh);
+      const float fc = pow5(1.0f - sm.vh);
+      const float3 F = F0 + (f3(1.f, 1.f, 1.f) - F0) * fc;
+      acc = acc + mul3(F, Li) * K;
+      if (kCid) {
+        const float pdf = ggx_D(sm.nh, rho) * sm.nh / (4.0f * sm.vh);
+        if (pdf > 0.0f && isfinite(pdf)) accd = accd + mul3(a, Li) * ((1.0f - m) * kInvPi * sm.nw / pdf);
+      }
+    }
+    if (A.hit_idx) A.hit_idx[p * spp + s] = q;
+  }
+  const float fs = (float)spp;
+  const float3 csm = f3(acc.x / fs, acc.y / fs, acc.z / fs);
+  const float3 cid = f3(accd.x / fs, accd.y / fs, accd.z / fs);
+  float3 fin = ld3(A.c_d + 3 * p) + csm;
+  if (kCid) fin = fin + cid;
+  st3(A.final_out + 3 * p, fin);
+  if (A.c_s_mc) st3(A.c_s_mc + 3 * p, csm);
+  if (A.c_id) st3(A.c_id + 3 * p, cid);
+  if (A.step_count && steps) atomicAdd(A.step_count, steps);
+}
+
+// ==========================================================================================
+// Backward (replay adjoint) and L2 loss
+// ==========================================================================================
+__device__ __forceinline__ void atomic_add3(float* p, float3 v) {
+  const unsigned act = __activemask();
+  const unsigned grp = __match_any_sync(act, (unsigned long long)p);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(grp) - 1;
+  unsigned rest = grp & ~(1u << leader);
+  float3 s = v;
+  while (rest) {
+    const int src = __ffs(rest) - 1;
+    rest &= rest - 1;
+    const float tx = __shfl_sync(grp, v.x, src), ty = __shfl_sync(grp, v.y, src), tz = __shfl_sync(grp, v.z, src);
+    if (lane == leader) s = s + f3(tx, ty, tz);
+  }
+  if (lane == leader) {
+    atomicAdd(p + 0, s.x);
+    atomicAdd(p + 1, s.y);
+    atomicAdd(p + 2, s.z);
+  }
+}
+
+// d ln G1(z; rho) / dz, / drho
+__device__ __forceinline__ void dlnG1(float z, float rho, float& dz, float& dr) {
+  const float a2 = rho * rho;
+  const float s = sqrtf(a2 + (1.0f - a2) * z * z);
+  dz = 1.0f / z - (1.0f + (1.0f - a2) * z / s) / (z + s);
+  dr = -(rho * (1.0f - z * z) / s) / (z + s);
+}
+
+// d ln D(c; rho) / dc, / drho with c = n.h
+__device__ __forceinline__ void dlnD(float c, float rho, float& dc, float& dr) {
+  const float a2 = rho * rho;
+  const float den = c * c * (a2 - 1.0f) + 1.0f;
+  dc = -4.0f * c * (a2 - 1.0f) / den;
+  dr = 2.0f / rho - 4.0f * rho * c * c / den;
+}
+
+// Scatter g (per channel) with weight `scale` through the bilinear taps into gm, and return
+// the derivatives of the bilinear value contracted with g along x and y (texel units).
+__device__ __forceinline__ void bilin_adj(const float* __restrict__ mips, const Taps& t, float3 g, float scale,
+                                          float* gm, float& gx, float& gy) {
+  const float3 a = ld3(mips + t.idx[0]), b = ld3(mips + t.idx[1]);
+  const float3 c = ld3(mips + t.idx[2]), d = ld3(mips + t.idx[3]);
+  gx = dot3(g, (b - a) * (1.0f - t.ty) + (d - c) * t.ty);
+  gy = dot3(g, (c - a) * (1.0f - t.tx) + (d - b) * t.tx);
+  if (scale != 0.0f) {
+    const float w00 = (1.0f - t.tx) * (1.0f - t.ty), w01 = t.tx * (1.0f - t.ty);
+    const float w10 = (1.0f - t.tx) * t.ty, w11 = t.tx * t.ty;
+    atomic_add3(gm + t.idx[0], g * (scale * w00));
+    atomic_add3(gm + t.idx[1], g * (scale * w01));
+    atomic_add3(gm + t.idx[2], g * (scale * w10));
+    atomic_add3(gm + t.idx[3], g * (scale * w11));
+  }
+}
+
+// Adjoint of SampleEnvMap(d, lambda): texel gradients into gm (all levels), returns d/dd and
+// d/dlambda (zero where lambda is clamped).
+__device__ __forceinline__ float3 env_lookup_adj(const float* __restrict__ mips, const EnvInfo& e, float3 d,
+                                                 float lam, float3 g, float* gm, float& glam) {
+  const float lmax = (float)(e.levels - 1);
+  const bool inside = lam > 0.0f && lam < lmax;
+  lam = fminf(fmaxf(lam, 0.0f), lmax);
+  const int l0 = (int)floorf(lam);
+  const int l1 = min(l0 + 1, e.levels - 1);
+  const float t = lam - (float)l0;
+  const DirAngles ang = dir_angles(d);
+  const Taps t0 = env_taps(e, l0, ang), t1 = env_taps(e, l1, ang);
+  float gx0, gy0, gx1 = 0.0f, gy1 = 0.0f;
+  bilin_adj(mips, t0, g, 1.0f - t, gm, gx0, gy0);
+  if (t != 0.0f) bilin_adj(mips, t1, g, t, gm, gx1, gy1);
+  const float gu = (1.0f - t) * gx0 * (float)e.w[l0] + t * gx1 * (float)e.w[l1];
+  const float gv = (1.0f - t) * gy0 * (float)e.h[l0] + t * gy1 * (float)e.h[l1];
+  glam = 0.0f;
+  if (inside && l1 != l0) glam = dot3(g, bilinear(mips, t1) - bilinear(mips, t0));
+  const float q2 = d.x * d.x + d.z * d.z;
+  if (!(q2 > 0.0f)) return f3(0.f, 0.f, 0.f);
+  const float q = sqrtf(q2);
+  const float r2 = q2 + d.y * d.y;
+  const float dux = -d.z * kInv2Pi / q2, duz = d.x * kInv2Pi / q2;
+  const float dvx = d.y * d.x * kInvPi / (q * r2), dvz = d.y * d.z * kInvPi / (q * r2), dvy = -q * kInvPi / r2;
+  return f3(gu * dux + gv * dvx, gv * dvy, gu * duz + gv * dvz);
+}
+
+__device__ __forceinline__ void bwd_mc_pixel(const FrameArgs& A, long long p) {
+  const long long HW = (long long)A.vs.H * A.vs.W;
+  const int view = (int)(p / HW);
+  const int rem = (int)(p - view * HW);
+  const int y = rem / A.vs.W, x = rem - y * A.vs.W;
+  float3 ga = f3(0.f, 0.f, 0.f), gn = f3(0.f, 0.f, 0.f);
+  float gr = 0.0f, gm = 0.0f;
+  const float z = __ldg(A.depth + p);
+  if (!is_background(z)) {
+    const DevCam& cam = A.vs.cam[view];
+    const float3 d = pix_dir_world(cam, x, y);
+    const float3 v = d * (-1.0f / sqrtf(dot3(d, d)));
+    const float3 n = ld3(A.normal + 3 * p);
+    const float nv = dot3(n, v);
+    const float rho = __ldg(A.rough + p), m = __ldg(A.metal + p);
+    const float3 a = ld3(A.albedo + 3 * p);
+    const float3 F0 = f3(f0_of(a.x, m), f0_of(a.y, m), f0_of(a.z, m));
+    const float3 gC = ld3(A.g_final + 3 * p) * (1.0f / (float)A.spp);
+    const float g1v = ggx_G1(nv, rho);
+    float dgv_z, dgv_r;
+    dlnG1(nv, rho, dgv_z, dgv_r);
+    const bool want_cid = (A.flags & SSGI_DIFFUSE_INDIRECT) != 0;
+    for (int s = 0; s < A.spp; ++s) {
+      const float2 xi = sample_uniforms(A.seed, view, (uint32_t)rem, (uint32_t)s);
+      const Sample sm = make_sample(n, v, nv, rho, xi);
+      if (!sm.valid) continue;
+      const int q = __ldg(A.hit_idx + p * A.spp + s);
+      if (q >= HW) continue;  // not an index this G-buffer's trace can produce
+      float3 Li;
+      Taps tm;
+      if (q >= 0) {
+        Li = ld3(A.c1 + 3 * (view * HW + q));
+      } else {
+        tm = env_taps(A.e, 0, dir_angles(sm.w));
+        Li = bilinear(A.mips, tm);
+      }
+      const float K = ggx_G1(sm.nw, rho) * g1v * sm.vh / (nv * sm.nh);
+      const float fc = pow5(1.0f - sm.vh);
+      const float3 F = F0 + (f3(1.f, 1.f, 1.f) - F0) * fc;
+      float3 gL = mul3(gC, F) * K;
+      const float3 gF = mul3(gC, Li) * K;
+      ga = ga + gF * (m * (1.0f - fc));
+      gm += dot3(gF, a - f3(0.04f, 0.04f, 0.04f)) * (1.0f - fc);
+      const float gKK = dot3(gC, mul3(F, Li)) * K;
+      float dgw_z, dgw_r;
+      dlnG1(sm.nw, rho, dgw_z, dgw_r);
+      float dlnK_r = dgw_r + dgv_r;
+      float3 dlnK_n = sm.w * dgw_z + v * (dgv_z - 1.0f / nv);
+      if (rho > 0.0f) {
+        float dd_c, dd_r;
+        dlnD(sm.nh, rho, dd_c, dd_r);
+        dlnK_r += dd_r;
+        dlnK_n = dlnK_n + sm.h * dd_c;
+      }
+      gr += gKK * dlnK_r;
+      gn = gn + dlnK_n * gKK;
+      if (want_cid) {
+        const float pdf = ggx_D(sm.nh, rho) * sm.nh / (4.0f * sm.vh);
+        if (pdf > 0.0f && isfinite(pdf)) {
+          const float kk = kInvPi / pdf;
+          ga = ga + mul3(gC, Li) * ((1.0f - m) * kk * sm.nw);
+          gm -= dot3(gC, mul3(a, Li)) * kk * sm.nw;
+          gn = gn + sm.w * (dot3(gC, mul3(a, Li)) * (1.0f - m) * kk);
+          gL = gL + mul3(gC, a) * ((1.0f - m) * kk * sm.nw);
+        }
+      }
+      if (q >= 0) {
+        atomic_add3(A.g_c1 + 3 * (view * HW + q), gL);
+      } else {
+        float gx, gy;
+        bilin_adj(A.mips, tm, gL, 1.0f, A.g_mips, gx, gy);
+      }
+    }
+  }
+  st3(A.g_albedo + 3 * p, ga);
+  st3(A.g_normal + 3 * p, gn);
+  A.g_rough[p] = gr;
+  A.g_metal[p] = gm;
+}
+
+__device__ __forceinline__ void bwd_direct_pixel(const FrameArgs& A, long long p) {
+  const long long HW = (long long)A.vs.H * A.vs.W;
+  const int view = (int)(p / HW);
+  const int rem = (int)(p - view * HW);
+  const int y = rem / A.vs.W, x = rem - y * A.vs.W;
+  const DevCam& cam = A.vs.cam[view];
+  const float3 d = pix_dir_world(cam, x, y);
+  const float3 gc1 = ld3(A.g_c1 + 3 * p);
+  const float3 gcd = ld3(A.g_final + 3 * p) + gc1;
+  const float3 gcs = gc1;
+  const float z = __ldg(A.depth + p);
+  if (is_background(z)) {
+    float gx, gy;
+    bilin_adj(A.mips, env_taps(A.e, 0, dir_angles(d)), gcd, 1.0f, A.g_mips, gx, gy);
+    return;
+  }
+  const float3 v = d * (-1.0f / sqrtf(dot3(d, d)));
+  const float3 n = ld3(A.normal + 3 * p);
+  const float nv = dot3(n, v);
+  const float mu = fminf(fmaxf(nv, 1e-4f), 1.0f);
+  const float3 r = n * (2.0f * nv) - v;
+  const float rho = __ldg(A.rough + p), m = __ldg(A.metal + p);
+  const float lmax = (float)(A.e.levels - 1);
+  const float lam = log2f(rho + 1.0f) * lmax;
+  const LutVal ab = lut_sample(A.lut, A.lut_n, rho, mu);
+  const float3 Er = env_lookup(A.mips, A.e, r, lam);
+  const float3 En = env_lookup(A.mips, A.e, n, lam);
+  const float3 a = ld3(A.albedo + 3 * p);
+  const float3 F0 = f3(f0_of(a.x, m), f0_of(a.y, m), f0_of(a.z, m));
+  const float3 ga = mul3(gcd, En) * (1.0f - m) + mul3(gcs, Er) * (ab.A * m);
+  const float gm = -dot3(gcd, mul3(a, En)) + dot3(gcs, mul3(Er, a - f3(0.04f, 0.04f, 0.04f))) * ab.A;
+  const float3 gEn = mul3(gcd, a) * (1.0f - m);
+  const float3 gEr = mul3(gcs, F0 * ab.A + f3(ab.B, ab.B, ab.B));
+  const float gA = dot3(gcs, mul3(Er, F0));
+  const float gB = dot3(gcs, Er);
+  float gl1, gl2;
+  const float3 gdn = env_lookup_adj(A.mips, A.e, n, lam, gEn, A.g_mips, gl1);
+  const float3 gdr = env_lookup_adj(A.mips, A.e, r, lam, gEr, A.g_mips, gl2);
+  float gnv = 0.0f;
+  if (nv > 1e-4f && nv < 1.0f) gnv = gA * ab.dA_dmu + gB * ab.dB_dmu;
+  // r = 2 (n.v) n - v
+  const float3 gn = gdn + v * (2.0f * dot3(gdr, n)) + gdr * (2.0f * nv) + v * gnv;
+  const float gr = gA * ab.dA_drho + gB * ab.dB_drho + (gl1 + gl2) * lmax / ((rho + 1.0f) * 0.69314718055994531f);
+  float* pa = A.g_albedo + 3 * p;
+  float* pn = A.g_normal + 3 * p;
+  st3(pa, ld3(pa) + ga);
+  st3(pn, ld3(pn) + gn);
+  A.g_rough[p] += gr;
+  A.g_metal[p] += gm;
+}
+
+__device__ __forceinline__ void bwd_env_item(const EnvInfo& e, const float* __restrict__ g_mips,
+                                             float* __restrict__ g_env, int t) {
+  const int w0 = e.w[0];
+  const int c = t % 3, j = (t / 3) % w0, i = t / (3 * w0);
+  float acc = 0.0f, scale = 1.0f;
+  for (int l = 0; l < e.levels; ++l) {
+    acc += scale * __ldg(g_mips + e.off[l] + ((i >> l) * e.w[l] + (j >> l)) * 3 + c);
+    scale *= 0.25f;
+  }
+  g_env[t] = acc;
+}
+
+__device__ __forceinline__ void l2_block(const float* __restrict__ f, const float* __restrict__ t, long long n,
+                                         float* __restrict__ g, float* __restrict__ loss, long long start,
+                                         long long stride) {
+  const float inv = 1.0f / (float)n;
+  float acc = 0.0f;
+  for (long long i = start + threadIdx.x; i < n; i += stride) {
+    const float r = __ldg(f + i) - __ldg(t + i);
+    g[i] = 2.0f * r * inv;
+    acc += r * r;
+  }
+  if (!loss) return;  // block-uniform
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ float part[8];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.0f;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += part[k];
+    atomicAdd(loss, s * inv);
+  }
+  __syncthreads();
+}
+
+}  // namespace ssgi

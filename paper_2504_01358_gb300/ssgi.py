@@ -241,6 +241,45 @@ def ssgi_backward_noalloc(g_final: torch.Tensor, g: GBuffer, cams, c1: torch.Ten
     return out
 
 
+def ssgi_step_fused_workspace_bytes(dims, env_h: int, env_w: int, hiz_levels: int) -> int:
+    V, H, W = dims
+    return N.lib().ssgi_step_fused_workspace_bytes(N.Dims(V, H, W), env_h, env_w, hiz_levels)
+
+
+def ssgi_step_fused(g: GBuffer, cams, env: torch.Tensor, lut: torch.Tensor, target: torch.Tensor,
+                    params: TraceParams, out: Optional[dict] = None, workspace: Optional[torch.Tensor] = None,
+                    stream=None) -> dict:
+    """One fused forward + L2 loss + backward launch over all views (outputs in a dict)."""
+    V, H, W = g.dims
+    dev = g.depth.device
+    he, we = int(env.shape[0]), int(env.shape[1])
+    if out is None:
+        out = {"final": torch.empty((V, H, W, 3), device=dev), "hit_idx": torch.empty((V, H, W, params.spp),
+               device=dev, dtype=torch.int32), "loss": torch.empty(1, device=dev),
+               "albedo": torch.empty((V, H, W, 3), device=dev), "rough": torch.empty((V, H, W), device=dev),
+               "metal": torch.empty((V, H, W), device=dev), "normal": torch.empty((V, H, W, 3), device=dev),
+               "env": torch.empty((he, we, 3), device=dev)}
+    nbytes = ssgi_step_fused_workspace_bytes((V, H, W), he, we, params.hiz_levels)
+    if workspace is None:
+        workspace = torch.empty(nbytes, device=dev, dtype=torch.uint8)
+    cam = cams if isinstance(cams, C.Array) else cameras(cams)
+    gs, ps = g.c_struct(), params.c_struct()
+    N.call("ssgi_step_fused", C.byref(gs), cam, _dev(env, "env"), he, we, _dev(lut, "lut"), int(lut.shape[0]),
+           _dev(target, "target"), C.byref(ps), _dev(out["final"], "final"), _dev(out["hit_idx"], "hit_idx", torch.int32),
+           _dev(out["loss"], "loss"), _dev(out["albedo"], "g_albedo"), _dev(out["rough"], "g_rough"),
+           _dev(out["metal"], "g_metal"), _dev(out["normal"], "g_normal"), _dev(out["env"], "g_env"),
+           _dev(workspace, "workspace", torch.uint8), workspace.numel(), _stream(stream))
+    out["_workspace"] = workspace
+    return out
+
+
+def ssgi_step_fused_check(workspace: torch.Tensor) -> bool:
+    """True if the last fused step on this workspace stopped at a grid barrier (synchronous)."""
+    f = C.c_int32()
+    N.call("ssgi_step_fused_check", _dev(workspace, "workspace", torch.uint8), C.byref(f))
+    return bool(f.value)
+
+
 # ------------------------------------------------------------------------------------------
 # autograd
 # ------------------------------------------------------------------------------------------

@@ -83,7 +83,7 @@ def assert_forward_parity(gpu, orc, label=""):
     assert np.all(margins < MARGIN_TOL), f"{label}: mismatch with decision margin {margins.max()}"
     pix_ok = ~bad.any(axis=-1)
     scale = np.maximum(np.abs(orc["final"]).max(axis=-1), RGB_FLOOR)
-    for key in ("final", "cs_mc", "c_id") if "c_id" in gpu else ("final", "cs_mc"):
+    for key in [k for k in ("final", "cs_mc", "c_id") if k in gpu]:
         okey = {"c_id": "cid"}.get(key, key)
         # error of each channel in units of the pixel's output RGB
         err = (np.abs(gpu[key].astype(np.float64) - orc[okey]).max(axis=-1) / scale)[pix_ok]
