@@ -223,6 +223,12 @@ ssgi_status ssgi_step_fused(const ssgi_gbuffer *g, const ssgi_camera *cams, cons
                             void *workspace, size_t ws_bytes, ssgi_stream_t stream);
 /* Synchronous: *failed = 1 if the last fused step on this workspace stopped at a barrier. */
 ssgi_status ssgi_step_fused_check(const void *workspace, int32_t *failed);
+/* Synchronous: the durations (ns, from %globaltimer) of the last fused step's phases as seen by
+ * its first block, in order: pyramids (env mips + Hi-Z, with the clears), direct shading,
+ * trace + loss, Monte-Carlo adjoint, direct adjoint, mip-chain adjoint (the last is block 0's
+ * own share only). */
+#define SSGI_FUSED_PHASES 6
+ssgi_status ssgi_step_fused_phase_ns(const void *workspace, uint64_t *ns);
 
 /* ---------------------------------------------------------------------------------------- */
 /* Serving: continuous batching of render requests (real-time relighting / material editing,  */

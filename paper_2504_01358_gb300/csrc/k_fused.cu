@@ -2,10 +2,16 @@
 // direct shading, trace with stored hits, L2 loss, backward) in a single persistent launch.
 //
 // The launch is cooperative, so every block is resident at once and the blocks may wait for
-// each other: the stages run as grid-stride phases separated by a grid barrier.  The barrier
-// is bounded: a block that waits longer than kBarrierSpinLimit sleeps marks the error word and
-// every block leaves; nothing spins forever.  The per-item code is the same as the stand-alone
-// kernels' (ssgi_ops.cuh), so the results match the per-stage path.
+// each other.  The step has five grid barriers, one per true all-to-all dependency:
+//   pyramids | shading | trace + loss | Monte-Carlo adjoint | direct adjoint | mip-chain adjoint
+// (shading reads any mip level; the trace reads any pixel's c1; the direct adjoint of a pixel
+// needs every receiver's scatter into its g_c1; the mip-chain adjoint needs every texel's
+// gradient).  Inside the pyramid phase the top levels are built by whichever block finishes
+// the last tile of a view (a counter, no waiting).  Work inside a phase is handed out from
+// counters, block by block.  The barrier is bounded: a block that waits longer than
+// kBarrierSpinLimit sleeps marks the error word and every block leaves; nothing spins forever.
+// The per-item code is the stand-alone kernels' (ssgi_ops.cuh), so the results match the
+// per-stage path bit for bit (gradients up to the order of atomic additions).
 #include <algorithm>
 #include <cstring>
 
@@ -15,6 +21,23 @@ namespace ssgi {
 
 constexpr int kFusedThreads = 128;                // one 8 x 16 trace tile per block iteration
 constexpr long long kBarrierSpinLimit = 1ll << 26;  // x ~100 ns sleeps: several seconds
+constexpr int kFusedBarBytes = 512;               // control block at the start of the workspace
+constexpr int kFusedStampOffset = 256;            // bytes into it: 64-bit phase timestamps
+
+// Control words (32-bit) of the control block.
+enum : int {
+  kArrive = 0,     // grid barrier: arrivals
+  kGen = 1,        // grid barrier: generation
+  kErr = 2,        // a block gave up waiting
+  kPyrNext = 3,    // next pyramid tile
+  kTraceNext = 4,  // next trace tile
+  kMcNext = 5,     // next Monte-Carlo adjoint chunk
+  kDirNext = 6,    // next direct adjoint chunk
+  kEnvDone = 7,    // environment tiles finished
+  kHizDone = 8,    // Hi-Z tiles finished, one word per view
+};
+static_assert((kHizDone + SSGI_MAX_VIEWS) * 4 <= kFusedStampOffset, "control words overlap the stamps");
+static_assert(kFusedStampOffset + 8 * (SSGI_FUSED_PHASES + 1) <= kFusedBarBytes, "stamps overflow");
 
 struct FusedArgs {
   FrameArgs f;
@@ -23,24 +46,64 @@ struct FusedArgs {
   float* hiz;        // workspace: the pyramid
   float* g_env;      // output
   float* loss;       // output (one float)
-  unsigned* bar;     // workspace: [0] arrivals, [1] generation, [2] error
+  unsigned* ctl;     // workspace: control block
   long long n_gc1;   // floats of g_c1
   int n_gmips;       // floats of g_mips
 };
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Block 0 records when it leaves barrier `k` (slot 0 = its start): the phase durations.
+__device__ __forceinline__ void stamp(unsigned* ctl, int k) {
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(ctl) + kFusedStampOffset)[k] = global_ns();
+}
+
+// Block-level dynamic work loop: the block takes chunk after chunk from `counter` (zero at the
+// start of the launch) until all `n` are taken; body(c) runs on every thread of the block.
+template <class Body>
+__device__ __forceinline__ void for_each_chunk(unsigned* counter, int n, Body body) {
+  __shared__ int s_c;
+  for (;;) {
+    if (threadIdx.x == 0) s_c = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int c = s_c;
+    __syncthreads();
+    if (c >= n) break;
+    body(c);
+  }
+}
+
+// Block-level: counts this block's finished piece of work on `counter`; true for the block that
+// finishes the last of `total` (its later loads see every other block's stores).
+__device__ __forceinline__ bool last_arrival(unsigned* counter, unsigned total) {
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == total - 1u;
+  __syncthreads();
+  const bool last = s_last != 0;
+  if (last) __threadfence();
+  return last;
+}
+
 // Grid barrier for a cooperative launch; returns false if any block gave up waiting.
-__device__ __forceinline__ bool grid_sync(unsigned* bar) {
+__device__ __forceinline__ bool grid_sync(unsigned* ctl) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = bar + 1;
-    volatile unsigned* verr = bar + 2;
+    volatile unsigned* vgen = ctl + kGen;
+    volatile unsigned* verr = ctl + kErr;
     const unsigned gen = *vgen;
     __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+    const unsigned arrived = atomicAdd(ctl + kArrive, 1u) + 1u;
     int ok = 1;
     if (arrived == gridDim.x) {
-      atomicExch(bar, 0u);
+      atomicExch(ctl + kArrive, 0u);
       __threadfence();
       atomicAdd(const_cast<unsigned*>(vgen), 1u);
     } else {
@@ -69,74 +132,88 @@ template <bool kCid>
 __global__ void __launch_bounds__(kFusedThreads, 8) k_step_fused(const __grid_constant__ FusedArgs F) {
   const FrameArgs& A = F.f;
   __shared__ int s_hoff[SSGI_MAX_HIZ_LEVELS], s_hw[SSGI_MAX_HIZ_LEVELS];
+  __shared__ TileBuf s_tile;
   if (threadIdx.x < SSGI_MAX_HIZ_LEVELS) {
     s_hoff[threadIdx.x] = A.hz.off[threadIdx.x];
     s_hw[threadIdx.x] = A.hz.w[threadIdx.x];
   }
   const int V = A.vs.V, H = A.vs.H, W = A.vs.W;
-  const long long npx = (long long)V * H * W;
+  const long long HW = (long long)H * W, npx = V * HW;
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long gsz = (long long)gridDim.x * blockDim.x;
   const EnvInfo& e = A.e;
+  unsigned* ctl = F.ctl;
+  stamp(ctl, 0);
 
-  // P0: clear the backward workspace and the loss; copy the base level into the mip chain
+  // P0: clear the backward accumulators and the loss; Hi-Z and environment pyramids, 32 x 32
+  // tiles through level 5, levels 6.. by the block that finishes a pyramid's last tile.
   for (long long i = gtid; i < F.n_gc1; i += gsz) A.g_c1[i] = 0.0f;
   for (long long i = gtid; i < F.n_gmips; i += gsz) A.g_mips[i] = 0.0f;
-  for (long long i = gtid; i < (long long)e.h[0] * e.w[0] * 3; i += gsz) F.mips[i] = __ldg(F.env + i);
   if (gtid == 0) *F.loss = 0.0f;
-  if (!grid_sync(F.bar)) return;
-
-  // P1: environment mips, one level per phase
-  for (int l = 1; l < e.levels; ++l) {
-    const int n = e.h[l] * e.w[l] * 3;
-    for (long long t = gtid; t < n; t += gsz) env_down_item(F.mips + e.off[l - 1], e.h[l - 1], e.w[l - 1], F.mips + e.off[l], (int)t);
-    if (!grid_sync(F.bar)) return;
-  }
-
-  // P2: Hi-Z, 32x32 tiles through level 5 (block-level), then the remaining levels
-  if (A.levels > 1) {
-    const int tx = (W + kHizTile - 1) / kHizTile, ty = (H + kHizTile - 1) / kHizTile;
-    for (int t = blockIdx.x; t < tx * ty * V; t += gridDim.x) {
-      const int v = t / (tx * ty), r = t - v * tx * ty;
-      hiz_tile_block(A.depth, H, W, A.hz, F.hiz, v, r % tx, r / tx);
-    }
-    if (!grid_sync(F.bar)) return;
-    for (int l = 6; l < A.levels; ++l) {
-      const long long n = (long long)V * A.hz.w[l] * A.hz.h[l];
-      for (long long t = gtid; t < n; t += gsz) hiz_level_item(A.hz, l, F.hiz, (int)t);
-      if (!grid_sync(F.bar)) return;
-    }
-  }
-
-  // P3: direct shading
-  for (long long p = gtid; p < npx; p += gsz) shade_pixel(A, p);
-  if (!grid_sync(F.bar)) return;
-
-  // P4: trace, one 8 x 16 tile per block iteration
   {
+    const int hx = (W + kHizTile - 1) / kHizTile, hy = (H + kHizTile - 1) / kHizTile;
+    const int n_hz = A.levels > 1 ? hx * hy * V : 0;
+    const int ex = e.w[0] / min(kHizTile, e.w[0]), ey = e.h[0] / min(kHizTile, e.h[0]);
+    for_each_chunk(ctl + kPyrNext, n_hz + ex * ey, [&](int t) {
+      if (t < n_hz) {
+        const int v = t / (hx * hy), r = t - v * hx * hy;
+        hiz_tile_block(A.depth, H, W, A.hz, F.hiz, v, r % hx, r / hx, s_tile);
+        if (A.levels > 6 && last_arrival(ctl + kHizDone + v, hx * hy)) hiz_upper_block(A.hz, v, F.hiz);
+      } else {
+        const int r = t - n_hz;
+        env_tile_block(F.env, e, F.mips, r % ex, r / ex, s_tile);
+        if (e.levels > 6 && last_arrival(ctl + kEnvDone, ex * ey)) env_upper_block(e, F.mips);
+      }
+    });
+  }
+  if (!grid_sync(ctl)) return;
+  stamp(ctl, 1);
+
+  // P1: direct shading
+  for (long long p = gtid; p < npx; p += gsz) shade_pixel(A, p);
+  if (!grid_sync(ctl)) return;
+  stamp(ctl, 2);
+
+  // P2: trace, one 8 x 16 tile per block iteration, and the L2 loss of each finished pixel.
+  // The per-tile cost varies by an order of magnitude (sky vs. rays that run out of steps),
+  // so blocks take the next tile from a counter instead of a fixed stride.
+  {
+    const float inv = 1.0f / (float)(npx * 3);
+    float acc = 0.0f;
     const int tx = (W + 7) / 8, ty = (H + 15) / 16;
-    for (int t = blockIdx.x; t < tx * ty * V; t += gridDim.x) {
+    for_each_chunk(ctl + kTraceNext, tx * ty * V, [&](int t) {
       const int v = t / (tx * ty), r = t - v * tx * ty;
       const int x = (r % tx) * 8 + (threadIdx.x % 8), y = (r / tx) * 16 + (threadIdx.x / 8);
-      if (x < W && y < H) trace_pixel<kCid>(A, x, y, v, s_hoff, s_hw);
-    }
+      if (x < W && y < H) {
+        const float3 fin = trace_pixel<kCid>(A, x, y, v, s_hoff, s_hw);
+        acc += l2_pixel(A, v * HW + (long long)y * W + x, fin, inv);
+      }
+    });
+    block_sum_add(acc, F.loss, inv);
   }
-  if (!grid_sync(F.bar)) return;
+  if (!grid_sync(ctl)) return;
+  stamp(ctl, 3);
 
-  // P5: L2 loss and its gradient
-  l2_block(A.final_out, A.target, npx * 3, A.g_final, F.loss, (long long)blockIdx.x * blockDim.x, gsz);
-  if (!grid_sync(F.bar)) return;
+  // P3: Monte-Carlo adjoint (scatters into g_c1 and g_mips)
+  const int nchunks = (int)((npx + kFusedThreads - 1) / kFusedThreads);
+  for_each_chunk(ctl + kMcNext, nchunks, [&](int c) {
+    const long long p = (long long)c * kFusedThreads + threadIdx.x;
+    if (p < npx) bwd_mc_pixel(A, p);
+  });
+  if (!grid_sync(ctl)) return;
+  stamp(ctl, 4);
 
-  // P6: Monte-Carlo adjoint (scatters into g_c1 and g_mips)
-  for (long long p = gtid; p < npx; p += gsz) bwd_mc_pixel(A, p);
-  if (!grid_sync(F.bar)) return;
+  // P4: direct-shading adjoint
+  for_each_chunk(ctl + kDirNext, nchunks, [&](int c) {
+    const long long p = (long long)c * kFusedThreads + threadIdx.x;
+    if (p < npx) bwd_direct_pixel(A, p);
+  });
+  if (!grid_sync(ctl)) return;
+  stamp(ctl, 5);
 
-  // P7: direct-shading adjoint
-  for (long long p = gtid; p < npx; p += gsz) bwd_direct_pixel(A, p);
-  if (!grid_sync(F.bar)) return;
-
-  // P8: mip-chain adjoint to the base texels
+  // P5: mip-chain adjoint to the base texels
   for (long long t = gtid; t < (long long)e.h[0] * e.w[0] * 3; t += gsz) bwd_env_item(e, A.g_mips, F.g_env, (int)t);
+  stamp(ctl, 6);
 }
 
 struct FusedLayout {
@@ -149,7 +226,7 @@ inline FusedLayout fused_layout(ssgi_dims d, int env_h, int env_w, int levels) {
   FusedLayout L;
   const size_t px = (size_t)d.views * d.height * d.width;
   size_t o = 0;
-  L.bar = o; o += 256;
+  L.bar = o; o += kFusedBarBytes;
   L.mips = o; o += up256(ssgi_env_mip_floats(env_h, env_w) * 4);
   L.hiz = o; o += up256(std::max<size_t>(ssgi_hiz_floats(d, levels), 1) * 4);
   L.cd = o; o += up256(px * 12);
@@ -198,7 +275,7 @@ ssgi_status ssgi_step_fused(const ssgi_gbuffer* g, const ssgi_camera* cams, cons
   F.hiz = (float*)(ws + L.hiz);
   F.g_env = g_env;
   F.loss = loss;
-  F.bar = (unsigned*)(ws + L.bar);
+  F.ctl = (unsigned*)(ws + L.bar);
   F.n_gc1 = npx * 3;
   F.n_gmips = (int)ssgi_env_mip_floats(env_h, env_w);
   A.depth = g->depth;
@@ -242,7 +319,7 @@ ssgi_status ssgi_step_fused(const ssgi_gbuffer* g, const ssgi_camera* cams, cons
     return SSGI_ERR_CUDA;
   const int blocks = per_sm * sms;
   cudaStream_t s = (cudaStream_t)stream;
-  if (cudaMemsetAsync(ws + L.bar, 0, 256, s) != cudaSuccess) return SSGI_ERR_CUDA;
+  if (cudaMemsetAsync(ws + L.bar, 0, kFusedBarBytes, s) != cudaSuccess) return SSGI_ERR_CUDA;
   void* args[] = {(void*)&F};
   if (cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(kFusedThreads), args, 0, s) != cudaSuccess) {
     cudaGetLastError();
@@ -253,9 +330,18 @@ ssgi_status ssgi_step_fused(const ssgi_gbuffer* g, const ssgi_camera* cams, cons
 
 ssgi_status ssgi_step_fused_check(const void* workspace, int32_t* failed) {
   if (!workspace || !failed) return SSGI_ERR_INVALID_ARG;
-  unsigned w[3];
+  unsigned w[kErr + 1];
   if (cudaMemcpy(w, workspace, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return SSGI_ERR_CUDA;
-  *failed = w[2] != 0;
+  *failed = w[kErr] != 0;
+  return SSGI_OK;
+}
+
+ssgi_status ssgi_step_fused_phase_ns(const void* workspace, uint64_t* ns) {
+  if (!workspace || !ns) return SSGI_ERR_INVALID_ARG;
+  unsigned long long t[SSGI_FUSED_PHASES + 1];
+  if (cudaMemcpy(t, (const char*)workspace + kFusedStampOffset, sizeof(t), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SSGI_ERR_CUDA;
+  for (int k = 0; k < SSGI_FUSED_PHASES; ++k) ns[k] = t[k + 1] >= t[k] ? t[k + 1] - t[k] : 0;
   return SSGI_OK;
 }
 

@@ -51,7 +51,8 @@ __global__ void k_env_down(const float* __restrict__ src, int hs, int ws, float*
 
 __global__ void __launch_bounds__(256) k_hiz_tile(const float* __restrict__ depth, int H, int W, HizInfo hz,
                                                   float* __restrict__ hiz) {
-  hiz_tile_block(depth, H, W, hz, hiz, blockIdx.z, blockIdx.x, blockIdx.y);
+  __shared__ TileBuf s;
+  hiz_tile_block(depth, H, W, hz, hiz, blockIdx.z, blockIdx.x, blockIdx.y, s);
 }
 
 __global__ void k_hiz_level(int V, HizInfo hz, int l, float* __restrict__ hiz) {

@@ -48,23 +48,26 @@ struct FrameArgs {
 // ==========================================================================================
 // Precomputation (Appendix C table, Sec. 3.2 mips, Sec. 3.3 pyramid)
 // ==========================================================================================
-__device__ __forceinline__ void env_down_item(const float* __restrict__ src, int hs, int ws, float* __restrict__ dst,
-                                              int t) {
+// The pyramid builders read the level below through ld.global.cg (L2, coherent): in the fused
+// step that level was written earlier in the same launch, possibly by another SM.
+__device__ __forceinline__ float env_avg4(float a, float b, float d, float e) { return 0.25f * (((a + b) + d) + e); }
+
+__device__ __forceinline__ void env_down_item(const float* src, int hs, int ws, float* dst, int t) {
   const int wd = ws >> 1;
   const int c = t % 3, j = (t / 3) % wd, i = t / (3 * wd);
-  const float a = src[((2 * i) * ws + 2 * j) * 3 + c], b = src[((2 * i) * ws + 2 * j + 1) * 3 + c];
-  const float d = src[((2 * i + 1) * ws + 2 * j) * 3 + c], e = src[((2 * i + 1) * ws + 2 * j + 1) * 3 + c];
-  dst[t] = 0.25f * (((a + b) + d) + e);
+  const float a = __ldcg(src + ((2 * i) * ws + 2 * j) * 3 + c), b = __ldcg(src + ((2 * i) * ws + 2 * j + 1) * 3 + c);
+  const float d = __ldcg(src + ((2 * i + 1) * ws + 2 * j) * 3 + c), e = __ldcg(src + ((2 * i + 1) * ws + 2 * j + 1) * 3 + c);
+  dst[t] = env_avg4(a, b, d, e);
 }
-
 
 constexpr int kHizTile = 32;  // level-0 pixels per block side; covers levels 1..5
 
+typedef float TileBuf[kHizTile][kHizTile + 1];
+
 // Block-level: every thread of the block calls it for the same tile (it synchronises the block);
-// the block has at least 128 threads.
+// the block has at least 128 threads; s is the block's shared tile buffer.
 __device__ __forceinline__ void hiz_tile_block(const float* __restrict__ depth, int H, int W, const HizInfo& hz,
-                                               float* __restrict__ hiz, int view, int tile_x, int tile_y) {
-  __shared__ float s[kHizTile][kHizTile + 1];
+                                               float* __restrict__ hiz, int view, int tile_x, int tile_y, TileBuf& s) {
   const int bx = tile_x * kHizTile, by = tile_y * kHizTile;
   const float* d0 = depth + (size_t)view * H * W;
   float* out = hiz + (size_t)view * hz.per_view;
@@ -111,13 +114,81 @@ __device__ __forceinline__ void hiz_level_item(const HizInfo& hz, int l, float* 
   const int i = rem / w, j = rem % w;
   const float* src = hiz + (size_t)view * hz.per_view + hz.off[l - 1];
   const int ws = hz.w[l - 1], hs = hz.h[l - 1];
-  float m = src[(2 * i) * ws + 2 * j];
-  if (2 * j + 1 < ws) m = fminf(m, src[(2 * i) * ws + 2 * j + 1]);
+  float m = __ldcg(src + (2 * i) * ws + 2 * j);
+  if (2 * j + 1 < ws) m = fminf(m, __ldcg(src + (2 * i) * ws + 2 * j + 1));
   if (2 * i + 1 < hs) {
-    m = fminf(m, src[(2 * i + 1) * ws + 2 * j]);
-    if (2 * j + 1 < ws) m = fminf(m, src[(2 * i + 1) * ws + 2 * j + 1]);
+    m = fminf(m, __ldcg(src + (2 * i + 1) * ws + 2 * j));
+    if (2 * j + 1 < ws) m = fminf(m, __ldcg(src + (2 * i + 1) * ws + 2 * j + 1));
   }
   hiz[(size_t)view * hz.per_view + hz.off[l] + rem] = m;
+}
+
+// Block-level: a 32 x 32 texel tile of the base environment level (tiles are exact: the sizes
+// are powers of two) copied into level 0 of the chain and reduced through level 5 in shared
+// memory, one channel at a time, with env_down_item's arithmetic.
+__device__ __forceinline__ void env_tile_block(const float* __restrict__ env0, const EnvInfo& e, float* mips,
+                                               int tile_x, int tile_y, TileBuf& s) {
+  const int w0 = e.w[0];
+  const int th = min(kHizTile, e.h[0]), tw = min(kHizTile, w0);
+  const int by = tile_y * th, bx = tile_x * tw;
+  for (int k = threadIdx.x; k < th * tw * 3; k += blockDim.x) {
+    const size_t o = ((size_t)(by + k / (tw * 3)) * w0 + bx) * 3 + k % (tw * 3);
+    mips[e.off[0] + o] = __ldg(env0 + o);
+  }
+  const int top = min(e.levels - 1, 5);
+  constexpr int kPer = (kHizTile / 2) * (kHizTile / 2) / 128;
+  for (int c = 0; c < 3; ++c) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < th * tw; k += blockDim.x)
+      s[k / tw][k % tw] = __ldg(env0 + ((size_t)(by + k / tw) * w0 + bx + k % tw) * 3 + c);
+    __syncthreads();
+    int nh = th, nw = tw;
+    for (int l = 1; l <= top; ++l) {
+      nh >>= 1;
+      nw >>= 1;
+      float m[kPer];
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        const int k = threadIdx.x + j * blockDim.x;
+        m[j] = 0.0f;
+        if (k < nh * nw) {
+          const int i = k / nw, q = k % nw;
+          m[j] = env_avg4(s[2 * i][2 * q], s[2 * i][2 * q + 1], s[2 * i + 1][2 * q], s[2 * i + 1][2 * q + 1]);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) {
+        const int k = threadIdx.x + j * blockDim.x;
+        if (k < nh * nw) {
+          const int i = k / nw, q = k % nw;
+          s[i][q] = m[j];
+          mips[e.off[l] + ((size_t)((by >> l) + i) * e.w[l] + (bx >> l) + q) * 3 + c] = m[j];
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Block-level: environment levels 6.. from level 5 (which is complete).
+__device__ __forceinline__ void env_upper_block(const EnvInfo& e, float* mips) {
+  for (int l = 6; l < e.levels; ++l) {
+    for (int t = threadIdx.x; t < e.h[l] * e.w[l] * 3; t += blockDim.x)
+      env_down_item(mips + e.off[l - 1], e.h[l - 1], e.w[l - 1], mips + e.off[l], t);
+    __threadfence();
+    __syncthreads();
+  }
+}
+
+// Block-level: Hi-Z levels 6.. of one view from its level 5 (which is complete).
+__device__ __forceinline__ void hiz_upper_block(const HizInfo& hz, int view, float* hiz) {
+  for (int l = 6; l < hz.levels; ++l) {
+    const int n = hz.w[l] * hz.h[l];
+    for (int t = threadIdx.x; t < n; t += blockDim.x) hiz_level_item(hz, l, hiz, view * n + t);
+    __threadfence();
+    __syncthreads();
+  }
 }
 
 // ==========================================================================================
@@ -265,7 +336,7 @@ __device__ __forceinline__ int march(const FrameArgs& A, const DevCam& c, const 
 // Trace all samples of pixel (x, y) of `view`: GGX sampling, march, gather, Monte-Carlo sum
 // and composite (one thread per pixel).
 template <bool kCid>
-__device__ __forceinline__ void trace_pixel(const FrameArgs& A, int x, int y, int view,
+__device__ __forceinline__ float3 trace_pixel(const FrameArgs& A, int x, int y, int view,
                                             const int* __restrict__ s_hoff, const int* __restrict__ s_hw) {
   const int W = A.vs.W, H = A.vs.H;
   const long long HW = (long long)H * W;
@@ -280,7 +351,7 @@ __device__ __forceinline__ void trace_pixel(const FrameArgs& A, int x, int y, in
     if (A.c_id) st3(A.c_id + 3 * p, f3(0.f, 0.f, 0.f));
     if (A.hit_idx)
       for (int s = 0; s < spp; ++s) A.hit_idx[p * spp + s] = SSGI_HIT_BACKGROUND;
-    return;
+    return v1;
   }
   const DevCam& cam = A.vs.cam[view];
   const bool brute = (A.flags & SSGI_BRUTE_FORCE) != 0;
@@ -330,6 +401,7 @@ __device__ __forceinline__ void trace_pixel(const FrameArgs& A, int x, int y, in
   if (A.c_s_mc) st3(A.c_s_mc + 3 * p, csm);
   if (A.c_id) st3(A.c_id + 3 * p, cid);
   if (A.step_count && steps) atomicAdd(A.step_count, steps);
+  return fin;
 }
 
 // ==========================================================================================
@@ -339,19 +411,38 @@ __device__ __forceinline__ void atomic_add3(float* p, float3 v) {
   const unsigned act = __activemask();
   const unsigned grp = __match_any_sync(act, (unsigned long long)p);
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(grp) - 1;
-  unsigned rest = grp & ~(1u << leader);
-  float3 s = v;
-  while (rest) {
-    const int src = __ffs(rest) - 1;
-    rest &= rest - 1;
-    const float tx = __shfl_sync(grp, v.x, src), ty = __shfl_sync(grp, v.y, src), tz = __shfl_sync(grp, v.z, src);
-    if (lane == leader) s = s + f3(tx, ty, tz);
+  if (grp == 0xffffffffu) {
+    // the whole warp adds to one texel (coarse mip levels): butterfly sum, one atomic per channel
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+      v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+      v.z += __shfl_xor_sync(0xffffffffu, v.z, o);
+    }
+    if (lane == 0) {
+      atomicAdd(p + 0, v.x);
+      atomicAdd(p + 1, v.y);
+      atomicAdd(p + 2, v.z);
+    }
+    return;
   }
-  if (lane == leader) {
-    atomicAdd(p + 0, s.x);
-    atomicAdd(p + 1, s.y);
-    atomicAdd(p + 2, s.z);
+  // lanes sharing an address form a list in lane order; pointer jumping doubles the span of
+  // each lane's suffix sum per step, so the group's first lane holds the total after at most
+  // five steps whatever the grouping
+  int nxt = __ffs(grp & ((0xffffffffu << lane) << 1)) - 1;
+  while (__any_sync(act, nxt >= 0)) {
+    const int src = nxt >= 0 ? nxt : lane;
+    const float tx = __shfl_sync(act, v.x, src), ty = __shfl_sync(act, v.y, src), tz = __shfl_sync(act, v.z, src);
+    const int nn = __shfl_sync(act, nxt, src);
+    if (nxt >= 0) {
+      v = v + f3(tx, ty, tz);
+      nxt = nn;
+    }
+  }
+  if (lane == __ffs(grp) - 1) {
+    atomicAdd(p + 0, v.x);
+    atomicAdd(p + 1, v.y);
+    atomicAdd(p + 2, v.z);
   }
 }
 
@@ -560,6 +651,22 @@ __device__ __forceinline__ void bwd_env_item(const EnvInfo& e, const float* __re
   g_env[t] = acc;
 }
 
+// Block-level: adds the block's sum of acc (one value per thread) times scale to *out.
+__device__ __forceinline__ void block_sum_add(float acc, float* out, float scale) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ float part[8];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.0f;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += part[k];
+    atomicAdd(out, s * scale);
+  }
+  __syncthreads();
+}
+
+// Block-level (blockDim <= 256): g = d/df of mean((f - t)^2) over n floats, loss += the mean.
 __device__ __forceinline__ void l2_block(const float* __restrict__ f, const float* __restrict__ t, long long n,
                                          float* __restrict__ g, float* __restrict__ loss, long long start,
                                          long long stride) {
@@ -571,17 +678,15 @@ __device__ __forceinline__ void l2_block(const float* __restrict__ f, const floa
     acc += r * r;
   }
   if (!loss) return;  // block-uniform
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  __shared__ float part[8];
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float s = 0.0f;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += part[k];
-    atomicAdd(loss, s * inv);
-  }
-  __syncthreads();
+  block_sum_add(acc, loss, inv);
+}
+
+// The same loss term for one pixel's final colour (already in registers); returns |r|^2.
+__device__ __forceinline__ float l2_pixel(const FrameArgs& A, long long p, float3 fin, float inv) {
+  const float3 t = ld3(A.target + 3 * p);
+  const float rx = fin.x - t.x, ry = fin.y - t.y, rz = fin.z - t.z;
+  st3(A.g_final + 3 * p, f3(2.0f * rx * inv, 2.0f * ry * inv, 2.0f * rz * inv));
+  return rx * rx + ry * ry + rz * rz;
 }
 
 }  // namespace ssgi

@@ -280,6 +280,16 @@ def ssgi_step_fused_check(workspace: torch.Tensor) -> bool:
     return bool(f.value)
 
 
+FUSED_PHASES = ("pyramids", "shade", "trace_loss", "bwd_mc", "bwd_direct", "bwd_env")
+
+
+def ssgi_step_fused_phase_ns(workspace: torch.Tensor) -> dict:
+    """Phase durations (ns) of the last fused step on this workspace, as seen by its first block."""
+    a = (C.c_uint64 * len(FUSED_PHASES))()
+    N.call("ssgi_step_fused_phase_ns", _dev(workspace, "workspace", torch.uint8), a)
+    return dict(zip(FUSED_PHASES, (int(x) for x in a)))
+
+
 # ------------------------------------------------------------------------------------------
 # autograd
 # ------------------------------------------------------------------------------------------

@@ -96,3 +96,10 @@ def test_serving_host_side_checks(N):
     assert L.ssgi_serve_submit(None, None, None) == 1
     assert L.ssgi_serve_poll(None, 1, None) == 1
     assert L.ssgi_serve_destroy(None, 0) == 1
+
+
+def test_fused_phase_names_match_the_header():
+    from paper_2504_01358_gb300 import ssgi
+    src = open(os.path.join(ROOT, "include", "ssgi.h")).read()
+    m = re.search(r"#define\s+SSGI_FUSED_PHASES\s+(\d+)", src)
+    assert m and int(m.group(1)) == len(ssgi.FUSED_PHASES)
