@@ -7,8 +7,11 @@ space trace -> L2 loss -> backward), every stage a libssgi.so call.
 
 Prints ONE JSON line (rank 0).  `value` is indirect rays per second through the whole step
 (V*H*W*spp rays / step time), all ranks together; each rank renders its own frame (weak
-scaling, no collective on the data path).  `--impl reference` times the FP64 CPU oracle on
-the same workload instead.
+scaling, no collective on the data path).  The line also carries the trace kernel's roofline
+(ALU-bound; L2 and HBM figures from the committed ncu summary and the library's own bandwidth
+probe), the end-to-end rate from pinned host buffers, the CPU oracle, the fused 8-view step
+(ssgi_step_fused, one launch) next to its per-stage equivalent, and the serving run.
+`--impl reference` times the FP64 CPU oracle on the same workload instead.
 """
 from __future__ import annotations
 
@@ -46,6 +49,7 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=400.0)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-fused", action="store_true")
     return ap.parse_args()
 
 
@@ -134,29 +138,111 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def kernel_source_hash() -> str:
+TRACE_SOURCES = ("k_trace.cu", "ssgi_ops.cuh", "ssgi_device.cuh", "ssgi_internal.h")
+TRACE_PROFILE = os.path.join(ROOT, "profiles", "k_trace_1600x900x16spp.txt")
+
+
+def kernel_source_hash(files=TRACE_SOURCES) -> str:
     h = hashlib.sha256()
-    for f in ("k_trace.cu", "ssgi_device.cuh", "ssgi_internal.h"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2504_01358_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """dram bytes per trace launch from the committed ncu summary, if taken on this source."""
-    path = os.path.join(ROOT, "profiles", "k_trace_1600x900x16spp.txt")
+def profile_summary(path=TRACE_PROFILE, files=TRACE_SOURCES):
+    """`key: value` lines of a committed ncu summary, or None if it was taken on other source."""
     try:
         kv = {}
         with open(path) as f:
             for line in f:
-                if ":" in line and not line.startswith(" "):
+                if ":" in line and not line.startswith((" ", "#")):
                     k, v = line.split(":", 1)
                     kv[k.strip()] = v.strip()
-        if kv.get("kernel_source_sha256_16") != kernel_source_hash():
-            return None
-        return float(kv["dram_bytes_per_launch"])
-    except (OSError, KeyError, ValueError):
+        return kv if kv.get("kernel_source_sha256_16") == kernel_source_hash(files) else None
+    except OSError:
         return None
+
+
+def profiled(kv, key):
+    try:
+        return float(kv[key]) if kv else None
+    except (KeyError, ValueError):
+        return None
+
+
+def probe_bandwidth():
+    """L2 and HBM read ceilings from the library's own probe (ssgi_read_bandwidth_probe)."""
+    import torch
+    import paper_2504_01358_gb300 as S
+    out = {}
+    for name, nbytes, reps in (("l2", 32 << 20, 64), ("hbm", 4 << 30, 1)):
+        buf = torch.empty(nbytes // 4, device="cuda", dtype=torch.float32).fill_(1.0)
+        sink = torch.zeros(1, device="cuda", dtype=torch.int32)
+        for _ in range(3):
+            S.ssgi_read_bandwidth_probe(buf, reps, sink)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            S.ssgi_read_bandwidth_probe(buf, reps, sink)
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        out[name + "_read_gbs"] = nbytes * reps / (min(ts) / 1e3) / 1e9
+        del buf
+    out["method"] = ("ssgi_read_bandwidth_probe: 16-byte ld.global.cg from 8 blocks x 256 threads per SM; "
+                     "l2 = a 32 MiB buffer read 64 times per launch, hbm = a 4 GiB buffer read once; best of 5")
+    return out
+
+
+def run_fused(steps: int, warmup: int):
+    """The multi-view step (8 views at 1245x825, 32 spp, one 512x1024 env) as one persistent
+    launch (ssgi_step_fused) and, for comparison, as the per-stage calls."""
+    import torch
+    import ssgi_inputs as si
+    import paper_2504_01358_gb300 as S
+    wl = si.config4()
+    V, H, W = wl.depth.shape
+    p = S.params_of(wl.params)
+    g, env, cams, tgt = S.to_device_workload(wl)
+    lut = S.ssgi_build_brdf_lut()
+    out = S.ssgi_step_fused(g, cams, env, lut, tgt, p)
+    ws = out["_workspace"]
+
+    def fused():
+        S.ssgi_step_fused(g, cams, env, lut, tgt, p, out=out, workspace=ws)
+
+    pipe = S.FramePipeline((V, H, W), wl.env.shape[:2], p, wl.cams, lut=lut)
+    pipe.load(wl)
+
+    def timed(fn):
+        for _ in range(max(warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.mean(ts)
+
+    f_ms = timed(fused)
+    if S.ssgi_step_fused_check(ws):
+        raise RuntimeError("fused step stopped at a grid barrier")
+    phases = {k: v / 1e6 for k, v in S.ssgi_step_fused_phase_ns(ws).items()}
+    s_ms = timed(pipe.step)
+    rays = V * H * W * p.spp
+    return {"workload": f"{V} views x {W}x{H}, {p.spp} spp, 60-box scene on a ring of cameras, env "
+                        f"{wl.env.shape[1]}x{wl.env.shape[0]}, forward + L2 loss + backward",
+            "fused_ms": f_ms, "fused_rays_per_s": rays / (f_ms / 1e3), "fused_launches_per_step": 1,
+            "fused_phase_ms": phases, "per_stage_ms": s_ms, "per_stage_rays_per_s": rays / (s_ms / 1e3),
+            "per_stage_launches_per_step": pipe.kernels_per_step(), "steps": steps,
+            "inputs": "G-buffer 296 MB + hit indices 1.05 GB per step: larger than L2, no flush needed"}
 
 
 # ----------------------------------------------------------------------------------------------
@@ -173,16 +259,36 @@ def oracle_step(wl, lut):
 
 
 def cpu_baseline(wl):
+    """The oracle on the host cores: five whole steps at all cores, then the trace stage of a
+    seeded 65,536-pixel sample at one thread (the same binary, FP64)."""
+    import numpy as np
     import oracle as O
     lut = O.build_lut()
+    cores = O.max_threads()
+    reps = 5
     t0 = time.perf_counter()
-    oracle_step(wl, lut)
-    dt = time.perf_counter() - t0
+    for _ in range(reps):
+        r = oracle_step(wl, lut)
+    dt = (time.perf_counter() - t0) / reps
     V, H, W = wl.depth.shape
-    rays = V * H * W * wl.params.spp
-    return {"value": rays / dt, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
-            "sample": f"one whole step of the same workload ({rays} rays: FP64 direct shading, Hi-Z, trace, "
-                      f"Monte-Carlo sum and adjoint, OpenMP over pixels), {dt:.2f} s wall"}
+    p = wl.params
+    rays = V * H * W * p.spp
+    pl = np.sort(np.random.default_rng(7).choice(V * H * W, size=65536, replace=False))
+    He, We = wl.env.shape[:2]
+    O.set_threads(1)
+    try:
+        t1 = time.perf_counter()
+        O.trace(wl.depth, wl.normal, wl.albedo, wl.rough, wl.metal, wl.cams, r["mips"], He, We, r["hiz"], r["c1"],
+                r["cd"], p.spp, p.max_steps, p.hiz_levels, p.thickness, p.max_distance, p.seed, p.flags, pix_list=pl)
+        dt1 = time.perf_counter() - t1
+    finally:
+        O.set_threads(cores)
+    return {"value": rays / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{reps} whole steps of the same workload ({rays} rays each: FP64 direct shading, Hi-Z, "
+                      f"trace, Monte-Carlo sum and adjoint, OpenMP over pixels), {dt:.2f} s wall per step",
+            "single_thread": {"value": len(pl) * p.spp / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"trace stage only (march + Monte-Carlo sum) of 65536 seeded random pixels "
+                                        f"x {p.spp} spp at one thread, {dt1:.2f} s wall"}}
 
 
 def run_reference(args):
@@ -472,7 +578,10 @@ def run_ours(args):
     alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / 1e9  # Gop/s
     alg_ops = OPS_PER_STEP * iters + OPS_PER_SAMPLE * valid
     achieved = alg_ops / (trace_ms / 1e3) / 1e9
-    traffic = profiled_traffic()
+    prof = profile_summary()
+    traffic = profiled(prof, "dram_bytes_per_launch")
+    bw = probe_bandwidth()
+    l2_bytes = profiled(prof, "lts_bytes_per_launch")
     roofline = {"kernel": "k_trace (ssgi_trace_indirect)", "bound": "alu", "achieved": achieved, "peak": alu_peak,
                 "unit": "Gop/s", "frac": achieved / alu_peak, "traffic": traffic,
                 "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
@@ -480,14 +589,26 @@ def run_ours(args):
                 "work": f"{OPS_PER_STEP} ops x {iters} march iterations + {OPS_PER_SAMPLE} ops x {valid} traced samples",
                 "trace_ms": trace_ms, "march_iterations": iters, "traced_samples": valid,
                 "hbm_algorithmic_gbs": (V * H * W * (36 + 12 + 12) + 4 * V * H * W * p.spp) / (trace_ms / 1e3) / 1e9,
-                "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0))}
+                "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
+                "l2_achieved_gbs": None if l2_bytes is None else l2_bytes / (trace_ms / 1e3) / 1e9,
+                "l2_peak_gbs": bw["l2_read_gbs"],
+                "warp_execution_efficiency": profiled(prof, "warp_execution_efficiency"),
+                "profile": None if prof is None else os.path.relpath(TRACE_PROFILE, ROOT)}
+
+    fused = None
+    if rank == 0 and world == 1 and not args.no_fused:
+        del pipe
+        torch.cuda.empty_cache()
+        fused = run_fused(10, 3)
+        torch.cuda.empty_cache()
+        pipe = None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl)
     serving = None
     if rank == 0 and not args.no_serving:
-        del pipe
+        pipe = None
         torch.cuda.empty_cache()
         serving = run_serving(args.serve_requests, args.serve_rate, args.serve_slots, 100.0)
 
@@ -499,7 +620,8 @@ def run_ours(args):
                 "fwd_bwd_ms": ms, "trace_rays_per_s": rays / (trace_ms / 1e3),
                 "stage_ms": stage_ms, "wall_s": t_wall,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clocks, "serving": serving}
+                "gpu_launches": launches, "clocks": clocks, "bandwidth_probe": bw, "fused_step": fused,
+                "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -330,6 +330,17 @@ ssgi_status ssgi_backward_noalloc(const float *g_final, const ssgi_gbuffer *g, c
                                   float *g_rough, float *g_metal, float *g_normal, float *g_env,
                                   ssgi_stream_t stream);
 
+/* ---------------------------------------------------------------------------------------- */
+/* Measurement: a read-bandwidth probe.  Streams `bytes` of device memory at `buf` `reps` times */
+/* through L2 only (16-byte loads that skip L1), from every SM.  Timed with events around it,  */
+/* a buffer that fits in L2 gives the L2 read ceiling and a much larger one the HBM ceiling:   */
+/* the rooflines of kernels whose working set lives in L2.  buf: device, 16-byte aligned;      */
+/* bytes: a positive multiple of 16; reps >= 1; sink: one device word, written only in the    */
+/* rare case that keeps the loads from being optimised away.  Asynchronous on `stream`.        */
+/* ---------------------------------------------------------------------------------------- */
+ssgi_status ssgi_read_bandwidth_probe(const void *buf, size_t bytes, int32_t reps, uint32_t *sink,
+                                      ssgi_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

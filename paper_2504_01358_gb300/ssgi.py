@@ -290,6 +290,17 @@ def ssgi_step_fused_phase_ns(workspace: torch.Tensor) -> dict:
     return dict(zip(FUSED_PHASES, (int(x) for x in a)))
 
 
+def ssgi_read_bandwidth_probe(buf: torch.Tensor, reps: int, sink: Optional[torch.Tensor] = None,
+                              stream=None) -> None:
+    """Streams the bytes of `buf` (a contiguous CUDA tensor) `reps` times through L2."""
+    if not (buf.is_cuda and buf.is_contiguous()):
+        raise ValueError("buf: contiguous CUDA tensor expected")
+    if sink is None:
+        sink = torch.zeros(1, device=buf.device, dtype=torch.int32)
+    N.call("ssgi_read_bandwidth_probe", C.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size(), int(reps),
+           _dev(sink, "sink", torch.int32), _stream(stream))
+
+
 # ------------------------------------------------------------------------------------------
 # autograd
 # ------------------------------------------------------------------------------------------

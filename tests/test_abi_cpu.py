@@ -103,3 +103,14 @@ def test_fused_phase_names_match_the_header():
     src = open(os.path.join(ROOT, "include", "ssgi.h")).read()
     m = re.search(r"#define\s+SSGI_FUSED_PHASES\s+(\d+)", src)
     assert m and int(m.group(1)) == len(ssgi.FUSED_PHASES)
+
+
+def test_bandwidth_probe_rejects_bad_arguments(N):
+    L = N.lib()
+    fake, sink = C.c_void_p(0x100000), C.c_void_p(0x200000)
+    assert L.ssgi_read_bandwidth_probe(None, 64, 1, sink, None) == 1
+    assert L.ssgi_read_bandwidth_probe(C.c_void_p(0x100008), 64, 1, sink, None) == 1  # not 16-byte aligned
+    assert L.ssgi_read_bandwidth_probe(fake, 60, 1, sink, None) == 1                  # not a multiple of 16
+    assert L.ssgi_read_bandwidth_probe(fake, 0, 1, sink, None) == 1
+    assert L.ssgi_read_bandwidth_probe(fake, 64, 0, sink, None) == 1
+    assert L.ssgi_read_bandwidth_probe(fake, 64, 1, None, None) == 1
