@@ -17,11 +17,12 @@ __all__ = [
     "build", "lib", "philox4x32_10", "ggx_D", "ggx_G1", "fresnel", "ggx_sample_h", "env_levels",
     "build_env_mips", "env_lookup", "build_lut", "lut_sample", "hiz_floats_per_view", "build_hiz",
     "shade_direct", "trace", "replay_final", "backward", "set_threads", "max_threads", "FLAG_DIFFUSE_INDIRECT",
-    "FLAG_BRUTE_FORCE", "MISS", "INVALID", "BACKGROUND", "forward", "hiz_levels_split", "LUT_N", "LUT_SAMPLES",
+    "FLAG_BRUTE_FORCE", "FLAG_PATHWISE", "MISS", "INVALID", "BACKGROUND", "forward", "hiz_levels_split", "LUT_N", "LUT_SAMPLES",
 ]
 
 FLAG_DIFFUSE_INDIRECT = 1
 FLAG_BRUTE_FORCE = 2
+FLAG_PATHWISE = 4
 MISS, INVALID, BACKGROUND = -1, -2, -3
 LUT_N = 64          # table resolution used by the presets
 LUT_SAMPLES = 4096  # Hammersley samples per table entry

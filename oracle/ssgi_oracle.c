@@ -29,6 +29,12 @@
  *   - Hit radiance is c1 of the hit pixel (first-pass radiance, nearest pixel).
  *   - Backward: hits, sampled directions and the sampling pdf are frozen ("replay mode");
  *     the paper only states that the march is not differentiable (Sec. 5).
+ *   - Pathwise backward (flag 4, answering the limitation stated in Sec. 5): the uniforms of
+ *     every sample and its hit index are frozen, the direction is re-drawn from the current
+ *     normal and roughness (reparameterised sampling), a hit keeps c1 of its frozen pixel and
+ *     a miss looks the environment up in the new direction.  Its n and rho derivatives are
+ *     taken here by central differences of that per-sample function (the definition of the
+ *     derivative, in FP64); everything else equals the replay adjoint at the base point.
  */
 #include <math.h>
 #include <stdint.h>
@@ -43,6 +49,7 @@
 
 #define ORF_DIFFUSE_INDIRECT 1u
 #define ORF_BRUTE_FORCE 2u
+#define ORF_PATHWISE 4u
 
 /* ------------------------------------------------------------------------------------------ */
 /* small vector helpers                                                                        */
@@ -739,12 +746,45 @@ int orc_trace(int V, int H, int W, const double *depth, const double *normal, co
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Pathwise (reparameterised) form of one Monte-Carlo summand (Sec. 3.3 estimator): with the   */
+/* sample's uniforms xi and hit index q fixed, the half vector and direction are drawn from the */
+/* given normal n and roughness rho, the weight is the cancelled f_s (n.w) / p_GGX(w) =          */
+/* F G1(n.w) G1(n.v) (v.h) / ((n.v)(n.h)) at those same n and rho, L = c1 of the frozen hit     */
+/* pixel (c1q) or the environment at mip 0 in the new direction.  spec and cid receive the      */
+/* specular summand F K L and the diffuse-indirect summand (1-m) a / pi L (n.w) / p per channel;  */
+/* returns 0 (and zeros) when the re-drawn sample is invalid.                                   */
+/* ------------------------------------------------------------------------------------------ */
+static int pathwise_summand(v3 n, double rho, v3 vv, const double xi[2], const double a[3], double m, int q,
+                            const double *c1q, const env_t *e, uint32_t flags, double spec[3], double cid[3]) {
+  double nv = dot(n, vv);
+  smp_t sm = make_sample(n, vv, nv, rho, xi);
+  for (int c = 0; c < 3; ++c) spec[c] = cid[c] = 0.0;
+  if (!sm.valid) return 0;
+  double L[3];
+  if (q >= 0) {
+    L[0] = c1q[0]; L[1] = c1q[1]; L[2] = c1q[2];
+  } else {
+    env_lookup(e, sm.w, 0.0, L);
+  }
+  double K = orc_ggx_G1(sm.nw, rho) * orc_ggx_G1(nv, rho) * sm.vh / (nv * sm.nh);
+  for (int c = 0; c < 3; ++c) spec[c] = K * orc_fresnel(f0_of(a[c], m), sm.vh) * L[c];
+  if (flags & ORF_DIFFUSE_INDIRECT) {
+    double pdf = orc_ggx_D(sm.nh, rho) * sm.nh / (4.0 * sm.vh);
+    if (pdf > 0.0 && isfinite(pdf))
+      for (int c = 0; c < 3; ++c) cid[c] = (1.0 - m) * a[c] / OR_PI * L[c] * sm.nw / pdf;
+  }
+  return 1;
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* Replay forward: the forward pass with the samples, their validity, the sampling pdf and the */
 /* hit pixels frozen at a base parameter set, evaluated at another parameter set.  Per sample   */
 /*   contribution = f_s(w; eval) (n.w) / p(w; base) * L(eval),  f_s = D F G / (4 (n.w)(n.v)),   */
 /* so that at eval == base it equals the forward pass.  This is the function whose derivative  */
 /* the backward pass computes (the march itself is not differentiable, Sec. 5).                 */
 /* Pixels whose base roughness is 0 (delta lobe) keep the cancelled form G (v.h)/((n.v)(n.h)). */
+/* With flag 4 (pathwise) a sample valid at the base is re-drawn at the evaluation normal and  */
+/* roughness instead (pathwise_summand); its hit index stays frozen.                           */
 /* ------------------------------------------------------------------------------------------ */
 int orc_replay_final(int V, int H, int W, const double *depth, const double *cams, int He, int We,
                      const double *lut, int lut_n, int spp, uint64_t seed, uint32_t flags,
@@ -783,6 +823,16 @@ int orc_replay_final(int V, int H, int W, const double *depth, const double *cam
         smp_t sm = make_sample(nb, vv, nvb, rb, xi);
         if (!sm.valid) continue;
         int q = hit_idx[p * spp + s];
+        if (flags & ORF_PATHWISE) {  /* direction re-drawn at the evaluation point */
+          double spec[3], cidv[3];
+          const double *c1q = q >= 0 ? c1 + 3 * ((long)v * H * W + q) : NULL;
+          pathwise_summand(ne, re, vv, xi, albedo_e + 3 * p, m, q, c1q, &e, flags, spec, cidv);
+          for (int c = 0; c < 3; ++c) {
+            acc[c] += spec[c];
+            accd[c] += cidv[c];
+          }
+          continue;
+        }
         double Li[3];
         if (q >= 0) {
           const double *src = c1 + 3 * ((long)v * H * W + q);
@@ -956,6 +1006,34 @@ int orc_backward(int V, int H, int W, const double *depth, const double *normal,
           gmt += gF * (a - 0.04) * (1.0 - fc);
           gK += gC * F * Li[c];
         }
+        const int pathwise = (flags & ORF_PATHWISE) != 0;
+        if (pathwise) {
+          /* d/d{n, rho} of the pathwise summand contracted with g_final / N: central differences */
+          const double hstep = 1e-6;
+          double gCv[3];
+          for (int c = 0; c < 3; ++c) gCv[c] = g_final[3 * p + c] / spp;
+          const double *c1q = q >= 0 ? c1 + 3 * ((long)v * H * W + q) : NULL;
+          double dth[4];
+          for (int k = 0; k < 4; ++k) {
+            double fpm[2];
+            for (int sg = 0; sg < 2; ++sg) {
+              double dlt = sg == 0 ? hstep : -hstep;
+              v3 nn = n;
+              double rr = rho;
+              if (k == 0) nn.x += dlt;
+              else if (k == 1) nn.y += dlt;
+              else if (k == 2) nn.z += dlt;
+              else rr += dlt;
+              double spec[3], cidv[3];
+              pathwise_summand(nn, rr, vv, xi, albedo + 3 * p, m, q, c1q, &e, flags, spec, cidv);
+              fpm[sg] = 0.0;
+              for (int c = 0; c < 3; ++c) fpm[sg] += gCv[c] * (spec[c] + cidv[c]);
+            }
+            dth[k] = (fpm[0] - fpm[1]) / (2.0 * hstep);
+          }
+          gn = add(gn, mk(dth[0], dth[1], dth[2]));
+          gr += dth[3];
+        }
         /* d ln K with K = D(n.h) G1(n.w) G1(n.v) / (4 (n.v) p_frozen) */
         double dgw_z, dgw_r, dgv_z, dgv_r;
         dlnG1(sm.nw, rho, &dgw_z, &dgw_r);
@@ -969,8 +1047,10 @@ int orc_backward(int V, int H, int W, const double *depth, const double *normal,
           dlnK_n = add(dlnK_n, scl(sm.h, dd_c));
         }
         double gKK = gK * K;
-        gr += gKK * dlnK_r;
-        gn = add(gn, scl(dlnK_n, gKK));
+        if (!pathwise) {
+          gr += gKK * dlnK_r;
+          gn = add(gn, scl(dlnK_n, gKK));
+        }
         if (flags & ORF_DIFFUSE_INDIRECT) {
           double pdf = orc_ggx_D(sm.nh, rho) * sm.nh / (4.0 * sm.vh);
           if (pdf > 0.0 && isfinite(pdf)) {
@@ -979,7 +1059,7 @@ int orc_backward(int V, int H, int W, const double *depth, const double *normal,
               double gC = g_final[3 * p + c] / spp;
               ga[c] += gC * (1.0 - m) / OR_PI * Li[c] * sm.nw / pdf;
               gmt -= gC * a / OR_PI * Li[c] * sm.nw / pdf;
-              gn = add(gn, scl(sm.w, gC * (1.0 - m) * a / OR_PI * Li[c] / pdf));
+              if (!pathwise) gn = add(gn, scl(sm.w, gC * (1.0 - m) * a / OR_PI * Li[c] / pdf));
               gL[c] += gC * (1.0 - m) * a / OR_PI * sm.nw / pdf;
             }
           }

@@ -358,3 +358,105 @@ def test_adjoint_matches_central_finite_differences(small, lut, flags):
         n_checked += 1
     errs = np.array(errs)
     assert np.max(errs) < 1e-2, (np.argmax(errs), np.max(errs))
+
+
+# --------------------------------------------------------------------------------------------
+# adjoint (pathwise mode: directions re-drawn from n and rho, hits frozen)
+# --------------------------------------------------------------------------------------------
+def test_pathwise_replay_at_the_base_point_is_the_forward_pass(small, lut):
+    for flags in (0, O.FLAG_DIFFUSE_INDIRECT):
+        r = O.forward(small, lut=lut, flags=flags)
+        f = _replay(small, lut, flags | O.FLAG_PATHWISE, small.normal, small.rough, small.normal, small.albedo,
+                    small.rough, small.metal, small.env, r["hit_idx"])
+        np.testing.assert_allclose(f, r["final"], rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("flags", [0, 1])
+def test_pathwise_adjoint_matches_central_finite_differences(small, lut, flags):
+    """The pathwise adjoint (flag 4) vs central differences of the pathwise replay forward over the
+    whole image: 256 random parameters over albedo, roughness, metallic, normal, env texels."""
+    w = small
+    fl = flags | O.FLAG_PATHWISE
+    r = O.forward(w, lut=lut, flags=flags)
+    target = w.target.astype(np.float64)
+    g_final = 2.0 * (r["final"] - target) / r["final"].size
+    He, We = w.env.shape[:2]
+    grads = O.backward(w.depth, w.normal, w.albedo, w.rough, w.metal, w.cams, r["mips"], He, We, lut, r["c1"],
+                       r["hit_idx"], g_final, w.params.spp, w.params.seed, fl)
+    base = {"albedo": w.albedo.astype(np.float64), "rough": w.rough.astype(np.float64),
+            "metal": w.metal.astype(np.float64), "normal": w.normal.astype(np.float64),
+            "env": w.env.astype(np.float64)}
+    rng = np.random.default_rng(300 + flags)
+    fg = np.argwhere(np.isfinite(w.depth))
+    kinds = ["albedo", "rough", "metal", "normal", "env"]
+    errs = []
+    while len(errs) < 256:
+        kind = kinds[len(errs) % 5]
+        if kind == "env":
+            idx = (rng.integers(0, He), rng.integers(0, We), rng.integers(0, 3))
+        else:
+            v, y, x = fg[rng.integers(0, len(fg))]
+            if kind == "normal" and abs(w.normal[v, y, x, 1]) > 0.999:
+                continue
+            idx = (v, y, x) if kind in ("rough", "metal") else (v, y, x, rng.integers(0, 3))
+        x0 = base[kind][idx]
+        h = 1e-6 * max(1.0, abs(x0))
+        vals = []
+        for sgn in (+1, -1):
+            p = {k: a.copy() for k, a in base.items()}
+            p[kind][idx] = x0 + sgn * h
+            f = _replay(w, lut, fl, base["normal"], base["rough"], p["normal"], p["albedo"], p["rough"], p["metal"],
+                        p["env"], r["hit_idx"])
+            vals.append(_loss(f, target))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        g = grads[kind][idx]
+        errs.append(abs(fd - g) / max(abs(fd), abs(g), 1e-7))
+    errs = np.array(errs)
+    assert np.max(errs) < 1e-2, (np.argmax(errs), np.max(errs))
+
+
+@pytest.mark.parametrize("flags", [0, O.FLAG_PATHWISE])
+def test_furnace_gradient_is_the_derivative_of_the_split_sum_integral(flags):
+    """Unbiasedness of both adjoints.  One pixel under a uniform environment L with every ray a
+    miss: E[c_s'] = L (F0 A(rho, mu) + B(rho, mu)) (Appendix C), so the expected roughness
+    gradient is L d/drho (F0 A + B) and the expected normal gradient along the tangent towards v
+    is L d/dmu (F0 A + B) (t.v); A, B come from a sampling-free quadrature.  8 seeds x 4096
+    samples; the mean must lie within 4 standard errors of the quadrature derivative."""
+    L = 1.3
+    cam = si.look_at((0.0, 1.0, 1.0), (0.0, 0.0, 0.0))
+    v = np.array([0.0, 1.0, 1.0]) / math.sqrt(2.0)
+    n = np.array([0.9, 0.45, -0.2])
+    n /= np.linalg.norm(n)
+    mu = float(n @ v)
+    rho, m = 0.45, 0.3
+    a = np.array([0.6, 0.3, 0.8])
+    g = np.array([0.3, 0.5, 0.2])
+    t1 = v - mu * n
+    t1 /= np.linalg.norm(t1)
+    t2 = np.cross(n, t1)
+    gr, gt1, gt2 = [], [], []
+    for seed in range(8):
+        params = si.TraceParams(spp=4096, max_steps=0, hiz_levels=1, seed=1000 + seed, flags=0)
+        wl = si.Workload("furnace", np.full((1, 1, 1), math.sqrt(2.0), np.float32),
+                         n.astype(np.float32).reshape(1, 1, 1, 3), a.astype(np.float32).reshape(1, 1, 1, 3),
+                         np.full((1, 1, 1), rho, np.float32), np.full((1, 1, 1), m, np.float32), cam[None],
+                         np.full((8, 16, 3), L, np.float32), params)
+        r = O.forward(wl, lut=O.build_lut(16, 256))
+        assert not (r["hit_idx"] >= 0).any()
+        gd = O.backward(wl.depth, wl.normal, wl.albedo, wl.rough, wl.metal, wl.cams, r["mips"], 8, 16,
+                        O.build_lut(16, 256), r["c1"], r["hit_idx"], g.reshape(1, 1, 1, 3), 4096, params.seed, flags)
+        gn = gd["normal"][0, 0, 0]
+        gr.append(gd["rough"][0, 0, 0])
+        gt1.append(gn @ t1)
+        gt2.append(gn @ t2)
+    F0 = 0.04 * (1 - m) + a * m
+    def S(r_, mu_):
+        A, B = _exact_split(r_, mu_)
+        return float(g @ (F0 * A + B)) * L
+    hr, hm = 2e-3, 2e-3
+    dS_dr = (S(rho + hr, mu) - S(rho - hr, mu)) / (2 * hr)
+    dS_dmu = (S(rho, mu + hm) - S(rho, mu - hm)) / (2 * hm)
+    for vals, expect in ((gr, dS_dr), (gt1, dS_dmu * float(t1 @ v)), (gt2, 0.0)):
+        vals = np.array(vals)
+        se = vals.std(ddof=1) / math.sqrt(len(vals))
+        assert abs(vals.mean() - expect) < 4 * se + 2e-3 * abs(expect) + 1e-5, (vals.mean(), expect, se)
