@@ -532,6 +532,30 @@ def run_ours(args):
     trace_ms = stage_ms["trace"]
     launches = pipe.kernels_per_step() * args.steps
 
+    # the pathwise adjoint (SSGI_PATHWISE) of the same frame next to the replay one (untimed in the step)
+    from paper_2504_01358_gb300._native import PATHWISE as N_PATHWISE
+    def adjoint_ms(flags):
+        saved = pipe.params.flags
+        pipe.params.flags = flags
+        try:
+            for _ in range(3):
+                pipe.adjoint()
+            ts = []
+            for k in range(10):
+                flush.fill_(float(k))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                pipe.adjoint()
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            return statistics.mean(ts)
+        finally:
+            pipe.params.flags = saved
+
+    adjoints = {"replay_ms": adjoint_ms(p.flags), "pathwise_ms": adjoint_ms(p.flags | N_PATHWISE),
+                "note": "ssgi_backward on the same frame and hit indices, 10 calls each, L2 flushed before each"}
+
     # march iterations of one trace launch (counted by the kernel itself, untimed)
     counter = torch.zeros(1, device="cuda", dtype=torch.int64)
     pipe.trace(step_count=counter)
@@ -620,7 +644,8 @@ def run_ours(args):
                 "fwd_bwd_ms": ms, "trace_rays_per_s": rays / (trace_ms / 1e3),
                 "stage_ms": stage_ms, "wall_s": t_wall,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clocks, "bandwidth_probe": bw, "fused_step": fused,
+                "gpu_launches": launches, "clocks": clocks, "bandwidth_probe": bw, "adjoint_modes": adjoints,
+                "fused_step": fused,
                 "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -77,6 +77,7 @@ typedef enum {
 /* ssgi_trace_params.flags */
 #define SSGI_DIFFUSE_INDIRECT 1u /* also estimate diffuse indirect light from the same rays and add it to final */
 #define SSGI_BRUTE_FORCE 2u      /* ignore the pyramid: walk every pixel, no step budget (reference mode) */
+#define SSGI_PATHWISE 4u         /* backward only: pathwise gradients through the sampled directions */
 
 typedef struct { int32_t views, height, width; } ssgi_dims;
 
@@ -109,7 +110,7 @@ typedef struct {
   float thickness;    /* a hit needs the ray to pass behind the depth buffer by at most this (world units) */
   float max_distance; /* ray length in world units (> 0) */
   uint64_t seed;      /* RNG key */
-  uint32_t flags;     /* SSGI_DIFFUSE_INDIRECT | SSGI_BRUTE_FORCE */
+  uint32_t flags;     /* SSGI_DIFFUSE_INDIRECT | SSGI_BRUTE_FORCE | SSGI_PATHWISE */
 } ssgi_trace_params;
 
 /* ---------------------------------------------------------------------------------------- */
@@ -188,6 +189,14 @@ ssgi_status ssgi_l2_loss(const float *final_in, const float *target, int64_t n, 
 /* sampled directions and the sampling pdf are frozen at their forward values ("replay"),  */
 /* and the adjoint is exact for that replay function:                                       */
 /*   per sample  f_s(w; theta) (n.w) / p_frozen * L(theta),  f_s = D F G / (4 (n.w)(n.v)).   */
+/* With SSGI_PATHWISE in params->flags (an answer to the limitation stated in Sec. 5) each    */
+/* sample's uniforms and hit index are frozen instead and its direction is re-drawn from the  */
+/* current normal and roughness (reparameterised sampling): per sample                        */
+/*   F G1(n.w) G1(n.v) (v.h) / ((n.v)(n.h)) * L,  h = h(n, rho, xi),  w = 2 (v.h) h - v,       */
+/* L = c1 of the frozen hit pixel or the environment (mip 0) in the re-drawn direction; the  */
+/* normal and roughness gradients then include d w / d{n, rho} (and the environment's        */
+/* variation along it).  Albedo, metallic, c1 and texel gradients are the same in both modes. */
+/* The forward ignores the flag.                                                              */
 /* ---------------------------------------------------------------------------------------- */
 /* Inputs: g_final = d loss / d final [V,H,W,3]; the forward's G-buffer, cameras, c1, env,
  * table, stored hit_idx [V,H,W,spp] and the same params.  Outputs (overwritten):

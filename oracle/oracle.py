@@ -16,7 +16,7 @@ import numpy as np
 __all__ = [
     "build", "lib", "philox4x32_10", "ggx_D", "ggx_G1", "fresnel", "ggx_sample_h", "env_levels",
     "build_env_mips", "env_lookup", "build_lut", "lut_sample", "hiz_floats_per_view", "build_hiz",
-    "shade_direct", "trace", "replay_final", "backward", "set_threads", "max_threads", "FLAG_DIFFUSE_INDIRECT",
+    "shade_direct", "trace", "replay_final", "backward", "set_threads", "set_pathwise_step", "max_threads", "FLAG_DIFFUSE_INDIRECT",
     "FLAG_BRUTE_FORCE", "FLAG_PATHWISE", "MISS", "INVALID", "BACKGROUND", "forward", "hiz_levels_split", "LUT_N", "LUT_SAMPLES",
 ]
 
@@ -88,6 +88,7 @@ def lib():
             L.orc_backward.argtypes = ([C.c_int] * 3 + [PD] * 7 + [C.c_int, C.c_int, PD, C.c_int, PD, PI32, PD,
                                        C.c_int, C.c_uint64, C.c_uint32] + [PD] * 5)
             L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_set_pathwise_step.argtypes = [D, C.c_int]
             L.orc_max_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -266,6 +267,12 @@ def backward(depth, normal, albedo, rough, metal, cams, mips, He, We, lut, c1, h
     if rc != 0:
         raise ValueError("orc_backward rejected its arguments")
     return {"albedo": ga, "rough": gr, "metal": gm, "normal": gn, "env": ge}
+
+
+def set_pathwise_step(h: float, mode: int = 0) -> None:
+    """Step (default 1e-6) and form (0 central, +1 forward, -1 backward) of the oracle's
+    differences for pathwise n / rho derivatives."""
+    lib().orc_set_pathwise_step(float(h), int(mode))
 
 
 def set_threads(n: int) -> None:

@@ -32,7 +32,8 @@
  *   - Pathwise backward (flag 4, answering the limitation stated in Sec. 5): the uniforms of
  *     every sample and its hit index are frozen, the direction is re-drawn from the current
  *     normal and roughness (reparameterised sampling), a hit keeps c1 of its frozen pixel and
- *     a miss looks the environment up in the new direction.  Its n and rho derivatives are
+ *     a miss looks the environment up in the new direction.  The sampling frame keeps the
+ *     branch (sign of n.z) of the base normal, so the summand is smooth in n at n.z = 0.  Its n and rho derivatives are
  *     taken here by central differences of that per-sample function (the definition of the
  *     derivative, in FP64); everything else equals the replay adjoint at the base point.
  */
@@ -50,6 +51,10 @@
 #define ORF_DIFFUSE_INDIRECT 1u
 #define ORF_BRUTE_FORCE 2u
 #define ORF_PATHWISE 4u
+/* difference step of the pathwise n / rho derivatives and its form: 0 central, +1 forward,
+ * -1 backward (orc_set_pathwise_step) */
+static double g_pathwise_h = 1e-6;
+static int g_pathwise_mode = 0;
 
 /* ------------------------------------------------------------------------------------------ */
 /* small vector helpers                                                                        */
@@ -127,20 +132,26 @@ static double f0_of(double a, double m) { return 0.04 * (1.0 - m) + a * m; }
  * distribution", Walter et al. 2007): cos^2(theta_h) = (1 - xi0) / (1 + (rho^2 - 1) xi0),
  * phi = 2 pi xi1, in the orthonormal basis of Duff et al. 2017 ("Building an Orthonormal
  * Basis, Revisited", JCGT 6(1)) around n. */
+static v3 ggx_sample_h_frame(v3 n, double sgn, double rho, double xi0, double xi1);
+
 void orc_ggx_sample_h(const double n_in[3], double rho, double xi0, double xi1, double h_out[3]) {
   v3 n = ld3(n_in);
+  v3 h = ggx_sample_h_frame(n, (n.z >= 0.0) ? 1.0 : -1.0, rho, xi0, xi1);
+  h_out[0] = h.x; h_out[1] = h.y; h_out[2] = h.z;
+}
+
+/* The same with the branch of the frame (the sign of n.z) given. */
+static v3 ggx_sample_h_frame(v3 n, double sgn, double rho, double xi0, double xi1) {
   double a2 = rho * rho;
   double c2 = (1.0 - xi0) / (1.0 + (a2 - 1.0) * xi0);
   double ct = sqrt(c2);
   double st = sqrt(fmax(0.0, 1.0 - c2));
   double phi = 2.0 * OR_PI * xi1;
-  double sgn = (n.z >= 0.0) ? 1.0 : -1.0;
   double aa = -1.0 / (sgn + n.z);
   double bb = n.x * n.y * aa;
   v3 t1 = mk(1.0 + sgn * n.x * n.x * aa, sgn * bb, -sgn * n.x);
   v3 t2 = mk(bb, sgn + n.y * n.y * aa, -n.y);
-  v3 h = add(add(scl(t1, st * cos(phi)), scl(t2, st * sin(phi))), scl(n, ct));
-  h_out[0] = h.x; h_out[1] = h.y; h_out[2] = h.z;
+  return add(add(scl(t1, st * cos(phi)), scl(t2, st * sin(phi))), scl(n, ct));
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -625,17 +636,19 @@ typedef struct {
   int valid;
 } smp_t;
 
-static smp_t make_sample(v3 n, v3 vv, double nv, double rho, const double xi[2]) {
+static smp_t make_sample_frame(v3 n, double sgn, v3 vv, double nv, double rho, const double xi[2]) {
   smp_t r;
-  double nn[3] = {n.x, n.y, n.z}, hh[3];
-  orc_ggx_sample_h(nn, rho, xi[0], xi[1], hh);
-  r.h = ld3(hh);
+  r.h = ggx_sample_h_frame(n, sgn, rho, xi[0], xi[1]);
   r.vh = dot(vv, r.h);
   r.w = sub(scl(r.h, 2.0 * r.vh), vv);
   r.nh = dot(n, r.h);
   r.nw = dot(n, r.w);
   r.valid = (nv > 0.0) && (r.nw > 0.0) && (r.vh > 0.0) && (r.nh > 0.0);
   return r;
+}
+
+static smp_t make_sample(v3 n, v3 vv, double nv, double rho, const double xi[2]) {
+  return make_sample_frame(n, (n.z >= 0.0) ? 1.0 : -1.0, vv, nv, rho, xi);
 }
 
 /* ------------------------------------------------------------------------------------------ */
@@ -752,12 +765,13 @@ int orc_trace(int V, int H, int W, const double *depth, const double *normal, co
 /* F G1(n.w) G1(n.v) (v.h) / ((n.v)(n.h)) at those same n and rho, L = c1 of the frozen hit     */
 /* pixel (c1q) or the environment at mip 0 in the new direction.  spec and cid receive the      */
 /* specular summand F K L and the diffuse-indirect summand (1-m) a / pi L (n.w) / p per channel;  */
-/* returns 0 (and zeros) when the re-drawn sample is invalid.                                   */
+/* returns 0 (and zeros) when the re-drawn sample is invalid.  sgn fixes the branch of the     */
+/* sampling frame (the sign of the base normal's z) so that the summand is smooth in n.        */
 /* ------------------------------------------------------------------------------------------ */
-static int pathwise_summand(v3 n, double rho, v3 vv, const double xi[2], const double a[3], double m, int q,
-                            const double *c1q, const env_t *e, uint32_t flags, double spec[3], double cid[3]) {
+static int pathwise_summand(v3 n, double sgn, double rho, v3 vv, const double xi[2], const double a[3], double m,
+                            int q, const double *c1q, const env_t *e, uint32_t flags, double spec[3], double cid[3]) {
   double nv = dot(n, vv);
-  smp_t sm = make_sample(n, vv, nv, rho, xi);
+  smp_t sm = make_sample_frame(n, sgn, vv, nv, rho, xi);
   for (int c = 0; c < 3; ++c) spec[c] = cid[c] = 0.0;
   if (!sm.valid) return 0;
   double L[3];
@@ -826,7 +840,8 @@ int orc_replay_final(int V, int H, int W, const double *depth, const double *cam
         if (flags & ORF_PATHWISE) {  /* direction re-drawn at the evaluation point */
           double spec[3], cidv[3];
           const double *c1q = q >= 0 ? c1 + 3 * ((long)v * H * W + q) : NULL;
-          pathwise_summand(ne, re, vv, xi, albedo_e + 3 * p, m, q, c1q, &e, flags, spec, cidv);
+          pathwise_summand(ne, nb.z >= 0.0 ? 1.0 : -1.0, re, vv, xi, albedo_e + 3 * p, m, q, c1q, &e, flags, spec,
+                           cidv);
           for (int c = 0; c < 3; ++c) {
             acc[c] += spec[c];
             accd[c] += cidv[c];
@@ -1009,7 +1024,7 @@ int orc_backward(int V, int H, int W, const double *depth, const double *normal,
         const int pathwise = (flags & ORF_PATHWISE) != 0;
         if (pathwise) {
           /* d/d{n, rho} of the pathwise summand contracted with g_final / N: central differences */
-          const double hstep = 1e-6;
+          const double hstep = g_pathwise_h;
           double gCv[3];
           for (int c = 0; c < 3; ++c) gCv[c] = g_final[3 * p + c] / spp;
           const double *c1q = q >= 0 ? c1 + 3 * ((long)v * H * W + q) : NULL;
@@ -1017,7 +1032,7 @@ int orc_backward(int V, int H, int W, const double *depth, const double *normal,
           for (int k = 0; k < 4; ++k) {
             double fpm[2];
             for (int sg = 0; sg < 2; ++sg) {
-              double dlt = sg == 0 ? hstep : -hstep;
+              double dlt = sg == 0 ? (g_pathwise_mode < 0 ? 0.0 : hstep) : (g_pathwise_mode > 0 ? 0.0 : -hstep);
               v3 nn = n;
               double rr = rho;
               if (k == 0) nn.x += dlt;
@@ -1025,11 +1040,12 @@ int orc_backward(int V, int H, int W, const double *depth, const double *normal,
               else if (k == 2) nn.z += dlt;
               else rr += dlt;
               double spec[3], cidv[3];
-              pathwise_summand(nn, rr, vv, xi, albedo + 3 * p, m, q, c1q, &e, flags, spec, cidv);
+              pathwise_summand(nn, n.z >= 0.0 ? 1.0 : -1.0, rr, vv, xi, albedo + 3 * p, m, q, c1q, &e, flags,
+                               spec, cidv);
               fpm[sg] = 0.0;
               for (int c = 0; c < 3; ++c) fpm[sg] += gCv[c] * (spec[c] + cidv[c]);
             }
-            dth[k] = (fpm[0] - fpm[1]) / (2.0 * hstep);
+            dth[k] = (fpm[0] - fpm[1]) / (g_pathwise_mode == 0 ? 2.0 * hstep : hstep);
           }
           gn = add(gn, mk(dth[0], dth[1], dth[2]));
           gr += dth[3];
@@ -1164,6 +1180,16 @@ int orc_backward(int V, int H, int W, const double *depth, const double *normal,
 /* ------------------------------------------------------------------------------------------ */
 /* threading control for timing                                                                */
 /* ------------------------------------------------------------------------------------------ */
+/* Step (default 1e-6) and form (0 central, default; +1 forward; -1 backward) of the
+ * differences of the pathwise derivatives.  Where the per-sample function is not
+ * differentiable (a sample on a bilinear texel-centre kink of the map, or on the edge of
+ * validity where the summand reaches 0 with a nonzero slope) the difference depends on the
+ * step and the one-sided differences disagree; comparing them finds those points. */
+void orc_set_pathwise_step(double h, int mode) {
+  if (h > 0.0) g_pathwise_h = h;
+  g_pathwise_mode = mode < 0 ? -1 : (mode > 0 ? 1 : 0);
+}
+
 void orc_set_threads(int n) {
 #ifdef _OPENMP
   if (n > 0) omp_set_num_threads(n);

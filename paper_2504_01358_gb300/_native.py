@@ -17,6 +17,7 @@ OK, INVALID_ARG, UNSUPPORTED, CUDA_ERR, OOM, BUDGET, QUEUE_FULL, TIMEOUT, NOT_RE
 HIT_MISS, HIT_INVALID, HIT_BACKGROUND = -1, -2, -3
 DIFFUSE_INDIRECT = 1
 BRUTE_FORCE = 2
+PATHWISE = 4
 
 STATUS = {
     0: "SSGI_OK", 1: "SSGI_ERR_INVALID_ARG", 2: "SSGI_ERR_UNSUPPORTED", 3: "SSGI_ERR_CUDA", 4: "SSGI_ERR_OOM",

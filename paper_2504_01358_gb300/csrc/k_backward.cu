@@ -5,7 +5,8 @@
 // replayed contribution is  f_s(w; theta) (n.w) / p_frozen * L(theta)
 //   = D(n.h) G1(n.w) G1(n.v) / (4 (n.v) p_frozen) * F(a, m) * L,
 // whose value at the forward point equals G (v.h)/((n.v)(n.h)) F L (D cancels).  Kernels:
-//   k_bwd_mc      per receiver pixel: d/d{a, m, rho, n} of the Monte-Carlo sum; scatters
+//   k_bwd_mc      per receiver pixel: d/d{a, m, rho, n} of the Monte-Carlo sum (replay or, with
+//                 SSGI_PATHWISE, through the re-drawn directions); scatters
 //                 d/dc1 to the hit pixels and d/dL_E to level-0 environment texels (atomics);
 //   k_bwd_direct  per pixel: adjoint of c_d = (1-m) a L_E(n, lambda) and
 //                 c_s = L_E(r, lambda) (F0 A + B) with d/dc_d = g_final + g_c1, d/dc_s = g_c1;
@@ -17,10 +18,19 @@
 
 namespace ssgi {
 
+template <bool kPathwise>
 __global__ void __launch_bounds__(256, 4) k_bwd_mc(FrameArgs A) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= (long long)A.vs.V * A.vs.H * A.vs.W) return;
-  bwd_mc_pixel(A, p);
+  bwd_mc_pixel<kPathwise>(A, p);
+}
+
+// Monte-Carlo adjoint in the mode the flags select (replay or pathwise).
+inline void launch_bwd_mc(const FrameArgs& A, int blocks, cudaStream_t s) {
+  if (A.flags & SSGI_PATHWISE)
+    k_bwd_mc<true><<<blocks, 256, 0, s>>>(A);
+  else
+    k_bwd_mc<false><<<blocks, 256, 0, s>>>(A);
 }
 
 __global__ void __launch_bounds__(256) k_bwd_direct(FrameArgs A) {
@@ -93,7 +103,7 @@ ssgi_status ssgi_backward(const float* g_final, const ssgi_gbuffer* g, const ssg
   A.seed = p->seed;
   A.flags = p->flags;
   const int blocks = ceil_div(npx, 256);
-  k_bwd_mc<<<blocks, 256, 0, s>>>(A);
+  launch_bwd_mc(A, blocks, s);
   ssgi_status st = launch_status();
   if (st != SSGI_OK) return st;
   k_bwd_direct<<<blocks, 256, 0, s>>>(A);
@@ -177,7 +187,7 @@ extern "C" ssgi_status ssgi_backward_noalloc(const float* g_final, const ssgi_gb
   A.seed = p->seed;
   A.flags = p->flags;
   const int blocks = ceil_div(npx, 256);
-  k_bwd_mc<<<blocks, 256, 0, s>>>(A);
+  launch_bwd_mc(A, blocks, s);
   ssgi_status st = launch_status();
   if (st != SSGI_OK) return st;
   k_bwd_direct<<<blocks, 256, 0, s>>>(A);

@@ -128,7 +128,7 @@ __device__ __forceinline__ bool grid_sync(unsigned* ctl) {
   return s_ok != 0;
 }
 
-template <bool kCid>
+template <bool kCid, bool kPathwise>
 __global__ void __launch_bounds__(kFusedThreads, 8) k_step_fused(const __grid_constant__ FusedArgs F) {
   const FrameArgs& A = F.f;
   __shared__ int s_hoff[SSGI_MAX_HIZ_LEVELS], s_hw[SSGI_MAX_HIZ_LEVELS];
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kFusedThreads, 8) k_step_fused(const __grid_co
   const int nchunks = (int)((npx + kFusedThreads - 1) / kFusedThreads);
   for_each_chunk(ctl + kMcNext, nchunks, [&](int c) {
     const long long p = (long long)c * kFusedThreads + threadIdx.x;
-    if (p < npx) bwd_mc_pixel(A, p);
+    if (p < npx) bwd_mc_pixel<kPathwise>(A, p);
   });
   if (!grid_sync(ctl)) return;
   stamp(ctl, 4);
@@ -313,8 +313,9 @@ ssgi_status ssgi_step_fused(const ssgi_gbuffer* g, const ssgi_camera* cams, cons
       cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess)
     return SSGI_ERR_CUDA;
   if (!coop) return SSGI_ERR_UNSUPPORTED;
-  const bool cid = (p->flags & SSGI_DIFFUSE_INDIRECT) != 0;
-  const void* fn = cid ? (const void*)k_step_fused<true> : (const void*)k_step_fused<false>;
+  const bool cid = (p->flags & SSGI_DIFFUSE_INDIRECT) != 0, pw = (p->flags & SSGI_PATHWISE) != 0;
+  const void* fn = cid ? (pw ? (const void*)k_step_fused<true, true> : (const void*)k_step_fused<true, false>)
+                       : (pw ? (const void*)k_step_fused<false, true> : (const void*)k_step_fused<false, false>);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFusedThreads, 0) != cudaSuccess || per_sm < 1)
     return SSGI_ERR_CUDA;
   const int blocks = per_sm * sms;

@@ -116,6 +116,32 @@ __device__ __forceinline__ float3 ggx_sample_h(float3 n, float rho, float xi0, f
   return t1 * (st * cp) + t2 * (st * sp) + n * ct;
 }
 
+// Derivatives of ggx_sample_h's half vector at fixed uniforms with respect to n.x, n.y, n.z
+// (dh[0..2]; the components taken independently, as the formula is written) and rho (dh[3]).
+// With q = sqrt(xi0 / den): sin = rho q, d sin / d rho = q (1 - xi0) / den, and
+// d cos / d rho = -cos rho xi0 / den; the frame's derivatives follow from aa' = aa^2 (n.z).
+__device__ __forceinline__ void ggx_sample_h_jac(float3 n, float rho, float xi0, float xi1, float3 dh[4]) {
+  const float a2 = rho * rho;
+  const float den = fmaf(a2 - 1.0f, xi0, 1.0f);
+  const float ct = sqrtf((1.0f - xi0) / den);
+  const float q = sqrtf(xi0 / den);
+  const float st = rho * q;
+  float sp, cp;
+  sincospif(2.0f * xi1, &sp, &cp);
+  const float sgn = n.z >= 0.0f ? 1.0f : -1.0f;
+  const float aa = -1.0f / (sgn + n.z);
+  const float aa2 = aa * aa;
+  const float bb = n.x * n.y * aa;
+  const float3 t1 = f3(1.0f + sgn * n.x * n.x * aa, sgn * bb, -sgn * n.x);
+  const float3 t2 = f3(bb, sgn + n.y * n.y * aa, -n.y);
+  const float c1 = st * cp, c2 = st * sp;
+  dh[0] = f3(2.0f * sgn * n.x * aa, sgn * n.y * aa, -sgn) * c1 + f3(n.y * aa, 0.0f, 0.0f) * c2 + f3(ct, 0.0f, 0.0f);
+  dh[1] = f3(0.0f, sgn * n.x * aa, 0.0f) * c1 + f3(n.x * aa, 2.0f * n.y * aa, -1.0f) * c2 + f3(0.0f, ct, 0.0f);
+  dh[2] = f3(sgn * n.x * n.x * aa2, sgn * n.x * n.y * aa2, 0.0f) * c1 + f3(n.x * n.y * aa2, n.y * n.y * aa2, 0.0f) * c2 +
+          f3(0.0f, 0.0f, ct);
+  dh[3] = (t1 * cp + t2 * sp) * (q * (1.0f - xi0) / den) + n * (-ct * rho * xi0 / den);
+}
+
 struct Sample {
   float3 h, w;
   float vh, nh, nw;

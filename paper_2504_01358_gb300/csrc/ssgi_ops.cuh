@@ -508,6 +508,11 @@ __device__ __forceinline__ float3 env_lookup_adj(const float* __restrict__ mips,
   return f3(gu * dux + gv * dvx, gv * dvy, gu * duz + gv * dvz);
 }
 
+// Adjoint of one receiver pixel's Monte-Carlo sum.  kPathwise = false: replay (direction and
+// pdf frozen; d/d{n, rho} of f_s (n.w) / p_frozen).  kPathwise = true: the direction is a
+// function of (n, rho) at frozen uniforms (ggx_sample_h_jac), the weight is the cancelled
+// F G1 G1 (v.h) / ((n.v)(n.h)) and a miss's radiance follows the direction through the map.
+template <bool kPathwise>
 __device__ __forceinline__ void bwd_mc_pixel(const FrameArgs& A, long long p) {
   const long long HW = (long long)A.vs.H * A.vs.W;
   const int view = (int)(p / HW);
@@ -554,31 +559,64 @@ __device__ __forceinline__ void bwd_mc_pixel(const FrameArgs& A, long long p) {
       const float gKK = dot3(gC, mul3(F, Li)) * K;
       float dgw_z, dgw_r;
       dlnG1(sm.nw, rho, dgw_z, dgw_r);
-      float dlnK_r = dgw_r + dgv_r;
-      float3 dlnK_n = sm.w * dgw_z + v * (dgv_z - 1.0f / nv);
-      if (rho > 0.0f) {
-        float dd_c, dd_r;
-        dlnD(sm.nh, rho, dd_c, dd_r);
-        dlnK_r += dd_r;
-        dlnK_n = dlnK_n + sm.h * dd_c;
+      float dd_c = 0.0f, dd_r = 0.0f;
+      if (rho > 0.0f) dlnD(sm.nh, rho, dd_c, dd_r);
+      if (!kPathwise) {
+        float dlnK_r = dgw_r + dgv_r;
+        float3 dlnK_n = sm.w * dgw_z + v * (dgv_z - 1.0f / nv);
+        if (rho > 0.0f) {
+          dlnK_r += dd_r;
+          dlnK_n = dlnK_n + sm.h * dd_c;
+        }
+        gr += gKK * dlnK_r;
+        gn = gn + dlnK_n * gKK;
       }
-      gr += gKK * dlnK_r;
-      gn = gn + dlnK_n * gKK;
+      float gcid = 0.0f;  // d loss / d ln(n.w / pdf) of the diffuse-indirect summand
       if (want_cid) {
         const float pdf = ggx_D(sm.nh, rho) * sm.nh / (4.0f * sm.vh);
         if (pdf > 0.0f && isfinite(pdf)) {
           const float kk = kInvPi / pdf;
           ga = ga + mul3(gC, Li) * ((1.0f - m) * kk * sm.nw);
           gm -= dot3(gC, mul3(a, Li)) * kk * sm.nw;
-          gn = gn + sm.w * (dot3(gC, mul3(a, Li)) * (1.0f - m) * kk);
+          if (!kPathwise) gn = gn + sm.w * (dot3(gC, mul3(a, Li)) * (1.0f - m) * kk);
           gL = gL + mul3(gC, a) * ((1.0f - m) * kk * sm.nw);
+          gcid = dot3(gC, mul3(a, Li)) * (1.0f - m) * kk * sm.nw;
         }
       }
+      float3 gdir = f3(0.f, 0.f, 0.f);  // d loss / d w through a miss's lookup
       if (q >= 0) {
         atomic_add3(A.g_c1 + 3 * (view * HW + q), gL);
+      } else if (kPathwise) {
+        float glam;
+        gdir = env_lookup_adj(A.mips, A.e, sm.w, 0.0f, gL, A.g_mips, glam);
       } else {
         float gx, gy;
         bilin_adj(A.mips, tm, gL, 1.0f, A.g_mips, gx, gy);
+      }
+      if (kPathwise) {
+        // total derivative through h(n, rho), w = 2 (v.h) h - v and the dot products
+        float3 dh[4];
+        ggx_sample_h_jac(n, rho, xi.x, xi.y, dh);
+        const float om = 1.0f - sm.vh, om2 = om * om;
+        const float gFdvh = -5.0f * om2 * om2 * dot3(mul3(gC, Li), f3(1.f, 1.f, 1.f) - F0) * K;
+        float gth[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float dvh = dot3(v, dh[k]);
+          const float3 dw = sm.h * (2.0f * dvh) + dh[k] * (2.0f * sm.vh);
+          const float en_h = k == 0 ? sm.h.x : (k == 1 ? sm.h.y : (k == 2 ? sm.h.z : 0.0f));
+          const float en_w = k == 0 ? sm.w.x : (k == 1 ? sm.w.y : (k == 2 ? sm.w.z : 0.0f));
+          const float dnv = k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : 0.0f));
+          const float dnh = dot3(n, dh[k]) + en_h;
+          const float dnw = dot3(n, dw) + en_w;
+          const float dr = k == 3 ? 1.0f : 0.0f;
+          const float dlnK = dgw_z * dnw + dgv_z * dnv + (dgw_r + dgv_r) * dr + dvh / sm.vh - dnv / nv - dnh / sm.nh;
+          float g = gKK * dlnK + gFdvh * dvh + dot3(gdir, dw);
+          if (gcid != 0.0f) g += gcid * (dnw / sm.nw + dvh / sm.vh - dd_c * dnh - dd_r * dr - dnh / sm.nh);
+          gth[k] = g;
+        }
+        gn = gn + f3(gth[0], gth[1], gth[2]);
+        gr += gth[3];
       }
     }
   }

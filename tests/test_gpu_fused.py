@@ -48,7 +48,7 @@ def _compare(a, b):
         assert float(np.abs(a[k] - b[k]).max()) / scale <= 1e-4, k
 
 
-@pytest.mark.parametrize("flags", [0, 1])
+@pytest.mark.parametrize("flags", [0, 1, 4, 5])
 def test_fused_step_equals_the_per_stage_path(flags):
     import paper_2504_01358_gb300 as S
     scene = si.make_scene(31, 10, 4.0, 1)

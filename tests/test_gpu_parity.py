@@ -211,6 +211,62 @@ def test_backward_matches_oracle_adjoint(S, olut, request, name, flags):
     assert rel <= GRAD_RTOL, ("env", rel)
 
 
+@pytest.mark.parametrize("flags", [0, 1])
+@pytest.mark.parametrize("name", ["small", "cfg1"])
+def test_pathwise_backward_matches_oracle_adjoint(S, olut, request, name, flags):
+    """SSGI_PATHWISE: directions re-drawn from (n, rho) at frozen uniforms, hits frozen.  Albedo,
+    metallic and texel gradients as in replay mode (same bound).  Normal and roughness gradients
+    against the oracle's FP64 central differences of the per-sample summand, 1e-3 of the scale on
+    every element where the summand is differentiable; a point where it is not (a sample on a
+    bilinear kink of the map, a texel centre, or on the edge of validity) shows up as a change
+    of the oracle's difference with its step (1e-6 vs 1e-7) or as forward and backward
+    differences that disagree, and is left out (<= 0.1 % of the elements)."""
+    wl = request.getfixturevalue(name)
+    if wl.target is None:
+        wl = dataclasses.replace(wl, target=si.uniform_target(99, *wl.depth.shape))
+    fl = flags | O.FLAG_PATHWISE
+    ggpu, gorc, aff = _backward_pair(S, wl, olut, fl)
+    ok = ~aff
+    for k in ("albedo", "metal"):
+        a, b = ggpu[k][ok], gorc[k][ok]
+        assert np.abs(a - b).max() / np.abs(b).max() <= GRAD_RTOL, k
+    a, b = ggpu["env"], gorc["env"]
+    assert np.linalg.norm(a - b) / np.linalg.norm(b) <= GRAD_RTOL, "env"
+    # the oracle's derivative at a second step and as one-sided differences: where they disagree
+    # the summand is not differentiable (a kink within the step of the base point)
+    r = orc_forward(wl, lut=olut, flags=flags)
+    g_final = (2.0 * (r["final"] - wl.target.astype(np.float64)) / r["final"].size).astype(np.float32)
+    He, We = wl.env.shape[:2]
+    alt = {}
+    try:
+        for key, h, mode in (("c7", 1e-7, 0), ("f7", 1e-7, 1), ("b7", 1e-7, -1)):
+            O.set_pathwise_step(h, mode)
+            alt[key] = O.backward(wl.depth, wl.normal, wl.albedo, wl.rough, wl.metal, wl.cams, r["mips"], He, We,
+                                  olut, r["c1"], r["hit_idx"], g_final, wl.params.spp, wl.params.seed, fl)
+    finally:
+        O.set_pathwise_step(1e-6, 0)
+    for k in ("rough", "normal"):
+        scale = np.abs(gorc[k][ok]).max()
+        kink = ((np.abs(gorc[k] - alt["c7"][k]) > 1e-4 * scale) |
+                (np.abs(alt["f7"][k] - alt["b7"][k]) > 1e-4 * scale))
+        if kink.ndim == ok.ndim + 1:  # per pixel
+            kink = kink.any(axis=-1)
+        sel = ok & ~kink
+        assert float(np.mean(kink[ok])) <= 1e-3, (k, "non-differentiable share", float(np.mean(kink[ok])))
+        err = np.abs(ggpu[k][sel] - gorc[k][sel]) / scale
+        assert err.max() <= GRAD_RTOL, (k, float(err.max()))
+
+
+def test_pathwise_differs_from_replay_only_in_normal_and_roughness(S, small, olut):
+    wl = dataclasses.replace(small, target=si.uniform_target(98, *small.depth.shape))
+    g0, _, _ = _backward_pair(S, wl, olut, 0)
+    g4, _, _ = _backward_pair(S, wl, olut, O.FLAG_PATHWISE)
+    for k in ("albedo", "metal", "env"):
+        np.testing.assert_allclose(g4[k], g0[k], rtol=0, atol=1e-6 * np.abs(g0[k]).max())
+    for k in ("rough", "normal"):
+        assert np.abs(g4[k] - g0[k]).max() > 1e-3 * np.abs(g0[k]).max(), k
+
+
 def test_autograd_function_matches_backward_call(S, small, olut):
     wl = small
     g, env, cams, tgt = S.to_device_workload(wl)
