@@ -16,7 +16,7 @@ import numpy as np
 __all__ = [
     "build", "lib", "philox4x32_10", "ggx_D", "ggx_G1", "fresnel", "ggx_sample_h", "env_levels",
     "build_env_mips", "env_lookup", "build_lut", "lut_sample", "hiz_floats_per_view", "build_hiz",
-    "shade_direct", "trace", "replay_final", "backward", "set_threads", "set_pathwise_step", "max_threads", "FLAG_DIFFUSE_INDIRECT",
+    "shade_direct", "depth_normals", "trace", "replay_final", "backward", "set_threads", "set_pathwise_step", "max_threads", "FLAG_DIFFUSE_INDIRECT",
     "FLAG_BRUTE_FORCE", "FLAG_PATHWISE", "MISS", "INVALID", "BACKGROUND", "forward", "hiz_levels_split", "LUT_N", "LUT_SAMPLES",
 ]
 
@@ -88,6 +88,7 @@ def lib():
             L.orc_backward.argtypes = ([C.c_int] * 3 + [PD] * 7 + [C.c_int, C.c_int, PD, C.c_int, PD, PI32, PD,
                                        C.c_int, C.c_uint64, C.c_uint32] + [PD] * 5)
             L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_depth_normals.argtypes = [C.c_int] * 3 + [PD, PD, PD]
             L.orc_set_pathwise_step.argtypes = [D, C.c_int]
             L.orc_max_threads.restype = C.c_int
             _lib = L
@@ -267,6 +268,16 @@ def backward(depth, normal, albedo, rough, metal, cams, mips, He, We, lut, c1, h
     if rc != 0:
         raise ValueError("orc_backward rejected its arguments")
     return {"albedo": ga, "rough": gr, "metal": gm, "normal": gn, "env": ge}
+
+
+def depth_normals(depth, cams) -> np.ndarray:
+    """World-space normals [V,H,W,3] from the depth buffer by finite differences (Sec. 3.1)."""
+    dep = _d(depth)
+    V, H, W = dep.shape
+    cm = _d(cams)
+    out = np.zeros((V, H, W, 3))
+    lib().orc_depth_normals(V, H, W, _p(dep), _p(cm), _p(out))
+    return out
 
 
 def set_pathwise_step(h: float, mode: int = 0) -> None:

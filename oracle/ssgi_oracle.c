@@ -630,6 +630,47 @@ static void march_init(march_t *M, const cam_t *cam, const double *depth_v, cons
 /* ------------------------------------------------------------------------------------------ */
 /* One sample's geometry: GGX half vector, reflected direction and validity (Sec. 3.3)          */
 /* ------------------------------------------------------------------------------------------ */
+/* ------------------------------------------------------------------------------------------ */
+/* Depth normals (Sec. 3.1, "depth normal": surface normals from the rendered depth buffer by   */
+/* finite differences, as in 2DGS).  P(x, y) = d(x, y) z(x, y) is the camera-space point of the */
+/* pixel centre at linear depth z.  Per direction the difference is central where both         */
+/* neighbours are foreground, one-sided where one is, absent where neither is.  The normal is   */
+/* normalize(dP/dy x dP/dx) (y down the image), flipped to face the camera, in world space.     */
+/* With a direction absent, or a zero cross product, it is the unit vector towards the camera.  */
+/* Background pixels get (0, 0, 0).                                                             */
+/* ------------------------------------------------------------------------------------------ */
+void orc_depth_normals(int V, int H, int W, const double *depth, const double *cams, double *normal_out) {
+  for (int v = 0; v < V; ++v) {
+    cam_t cam = cam_init(cams + 14 * v, H, W);
+    const double *dz = depth + (long)v * H * W;
+#pragma omp parallel for schedule(static)
+    for (int rem = 0; rem < H * W; ++rem) {
+      int y = rem / W, x = rem % W;
+      double *out = normal_out + 3 * ((long)v * H * W + rem);
+      out[0] = out[1] = out[2] = 0.0;
+      if (is_background(dz[rem])) continue;
+      v3 P = scl(pix_dir_cam(&cam, x, y), dz[rem]);
+      int l = (x > 0 && !is_background(dz[rem - 1])) ? x - 1 : x;
+      int r = (x + 1 < W && !is_background(dz[rem + 1])) ? x + 1 : x;
+      int u = (y > 0 && !is_background(dz[rem - W])) ? y - 1 : y;
+      int b = (y + 1 < H && !is_background(dz[rem + W])) ? y + 1 : y;
+      v3 n = scl(P, -1.0 / len(P));
+      if (l != r && u != b) {
+        v3 dPx = sub(scl(pix_dir_cam(&cam, r, y), dz[y * W + r]), scl(pix_dir_cam(&cam, l, y), dz[y * W + l]));
+        v3 dPy = sub(scl(pix_dir_cam(&cam, x, b), dz[b * W + x]), scl(pix_dir_cam(&cam, x, u), dz[u * W + x]));
+        v3 c = mk(dPy.y * dPx.z - dPy.z * dPx.y, dPy.z * dPx.x - dPy.x * dPx.z, dPy.x * dPx.y - dPy.y * dPx.x);
+        double cl = len(c);
+        if (cl > 0.0) {
+          n = scl(c, 1.0 / cl);
+          if (dot(n, P) > 0.0) n = scl(n, -1.0);
+        }
+      }
+      v3 nw = cam_to_world_dir(&cam, n);
+      out[0] = nw.x; out[1] = nw.y; out[2] = nw.z;
+    }
+  }
+}
+
 typedef struct {
   v3 h, w;            /* half vector, sampled direction (world) */
   double vh, nh, nw;  /* at the sampling normal */
