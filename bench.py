@@ -556,6 +556,23 @@ def run_ours(args):
     adjoints = {"replay_ms": adjoint_ms(p.flags), "pathwise_ms": adjoint_ms(p.flags | N_PATHWISE),
                 "note": "ssgi_backward on the same frame and hit indices, 10 calls each, L2 flushed before each"}
 
+    # depth normals of the same frame (Sec. 3.1; 4 B read + 12 B written per pixel, HBM-bound)
+    nrm = torch.empty_like(pipe.g.normal)
+    ts = []
+    for k in range(13):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        S.ssgi_depth_normals(pipe.g.depth, pipe.cam, out=nrm)
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    dn_ms = statistics.mean(ts[3:])
+    depth_normals = {"ms": dn_ms, "algorithmic_bytes": 16 * V * H * W,
+                     "achieved_gbs": 16 * V * H * W / (dn_ms / 1e3) / 1e9, "launches": 1,
+                     "note": "ssgi_depth_normals at the step's frame, L2 flushed before each of 10 timed calls"}
+    del nrm
+
     # march iterations of one trace launch (counted by the kernel itself, untimed)
     counter = torch.zeros(1, device="cuda", dtype=torch.int64)
     pipe.trace(step_count=counter)
@@ -645,6 +662,7 @@ def run_ours(args):
                 "stage_ms": stage_ms, "wall_s": t_wall,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "bandwidth_probe": bw, "adjoint_modes": adjoints,
+                "depth_normals": depth_normals,
                 "fused_step": fused,
                 "serving": serving}
         print(json.dumps(line), flush=True)

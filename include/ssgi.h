@@ -340,6 +340,19 @@ ssgi_status ssgi_backward_noalloc(const float *g_final, const ssgi_gbuffer *g, c
                                   ssgi_stream_t stream);
 
 /* ---------------------------------------------------------------------------------------- */
+/* Depth normals (Sec. 3.1 "depth normal": surface normals from the rendered depth buffer by  */
+/* finite differences, as in 2DGS).  P(x, y) = camera-space point of the pixel centre at its  */
+/* linear depth; per image direction a central difference where both neighbours are          */
+/* foreground, one-sided where one is; n = normalize(dP/dy x dP/dx) (y down the image),       */
+/* flipped to face the camera, in world space.  With no foreground neighbour in a direction   */
+/* (or a zero cross product) n is the unit vector towards the camera; background pixels get   */
+/* (0, 0, 0).  depth [V,H,W] and normal_out [V,H,W,3] are device arrays (distinct); cams: V    */
+/* host records.  Asynchronous on `stream`.                                                    */
+/* ---------------------------------------------------------------------------------------- */
+ssgi_status ssgi_depth_normals(const float *depth, ssgi_dims d, const ssgi_camera *cams, float *normal_out,
+                               ssgi_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Measurement: a read-bandwidth probe.  Streams `bytes` of device memory at `buf` `reps` times */
 /* through L2 only (16-byte loads that skip L1), from every SM.  Timed with events around it,  */
 /* a buffer that fits in L2 gives the L2 read ceiling and a much larger one the HBM ceiling:   */

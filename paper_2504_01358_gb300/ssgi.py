@@ -290,6 +290,16 @@ def ssgi_step_fused_phase_ns(workspace: torch.Tensor) -> dict:
     return dict(zip(FUSED_PHASES, (int(x) for x in a)))
 
 
+def ssgi_depth_normals(depth: torch.Tensor, cams, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """World-space normals [V,H,W,3] from a depth buffer [V,H,W] by finite differences."""
+    V, H, W = depth.shape
+    if out is None:
+        out = torch.empty((V, H, W, 3), device=depth.device, dtype=torch.float32)
+    cam = cams if isinstance(cams, C.Array) else cameras(cams)
+    N.call("ssgi_depth_normals", _dev(depth, "depth"), N.Dims(V, H, W), cam, _dev(out, "normal_out"), _stream(stream))
+    return out
+
+
 def ssgi_read_bandwidth_probe(buf: torch.Tensor, reps: int, sink: Optional[torch.Tensor] = None,
                               stream=None) -> None:
     """Streams the bytes of `buf` (a contiguous CUDA tensor) `reps` times through L2."""

@@ -114,3 +114,13 @@ def test_bandwidth_probe_rejects_bad_arguments(N):
     assert L.ssgi_read_bandwidth_probe(fake, 0, 1, sink, None) == 1
     assert L.ssgi_read_bandwidth_probe(fake, 64, 0, sink, None) == 1
     assert L.ssgi_read_bandwidth_probe(fake, 64, 1, None, None) == 1
+
+
+def test_depth_normals_rejects_bad_arguments(N):
+    L = N.lib()
+    fake = C.c_void_p(0x100000)
+    cams = (N.Camera * 1)()
+    assert L.ssgi_depth_normals(None, N.Dims(1, 8, 8), cams, fake, None) == 1
+    assert L.ssgi_depth_normals(fake, N.Dims(1, 8, 8), cams, None, None) == 1
+    assert L.ssgi_depth_normals(fake, N.Dims(0, 8, 8), cams, fake, None) == 1
+    assert L.ssgi_depth_normals(fake, N.Dims(1, 8, 8), None, fake, None) == 1
