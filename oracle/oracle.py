@@ -16,7 +16,7 @@ import numpy as np
 __all__ = [
     "build", "lib", "philox4x32_10", "ggx_D", "ggx_G1", "fresnel", "ggx_sample_h", "env_levels",
     "build_env_mips", "env_lookup", "build_lut", "lut_sample", "hiz_floats_per_view", "build_hiz",
-    "shade_direct", "depth_normals", "trace", "replay_final", "backward", "set_threads", "set_pathwise_step", "max_threads", "FLAG_DIFFUSE_INDIRECT",
+    "shade_direct", "depth_normals", "composite_gbuffer", "GBUFFER_KEYS", "trace", "replay_final", "backward", "set_threads", "set_pathwise_step", "max_threads", "FLAG_DIFFUSE_INDIRECT",
     "FLAG_BRUTE_FORCE", "FLAG_PATHWISE", "MISS", "INVALID", "BACKGROUND", "forward", "hiz_levels_split", "LUT_N", "LUT_SAMPLES",
 ]
 
@@ -268,6 +268,23 @@ def backward(depth, normal, albedo, rough, metal, cams, mips, He, We, lut, c1, h
     if rc != 0:
         raise ValueError("orc_backward rejected its arguments")
     return {"albedo": ga, "rough": gr, "metal": gm, "normal": gn, "env": ge}
+
+
+GBUFFER_KEYS = ("depth", "normal", "albedo", "rough", "metal")
+
+
+def composite_gbuffer(scene: dict, obj: dict):
+    """Object insertion (Sec. 4, "Object Insertion"): the object's G-buffer, rendered on its own,
+    is merged into the scene's by depth comparison.  A pixel takes all five of the object's
+    channels where the object's depth is strictly smaller (nearer) than the scene's; ties and
+    object background (+inf) keep the scene.  Returns (merged channels, mask of object pixels)."""
+    win = np.asarray(obj["depth"]) < np.asarray(scene["depth"])
+    out = {}
+    for k in GBUFFER_KEYS:
+        a, b = np.asarray(scene[k]), np.asarray(obj[k])
+        w = win[..., None] if a.ndim == win.ndim + 1 else win
+        out[k] = np.where(w, b, a)
+    return out, win
 
 
 def depth_normals(depth, cams) -> np.ndarray:
