@@ -340,6 +340,20 @@ ssgi_status ssgi_backward_noalloc(const float *g_final, const ssgi_gbuffer *g, c
                                   ssgi_stream_t stream);
 
 /* ---------------------------------------------------------------------------------------- */
+/* Object insertion (Sec. 4 "Object Insertion"): an object's G-buffer, rendered on its own,   */
+/* merged into the scene's by depth comparison (before the pyramid and shading).  A pixel     */
+/* takes all five of the object's channels where the object's depth is strictly smaller than  */
+/* the scene's; ties and object background (+inf) keep the scene.  scene and object: device   */
+/* G-buffers of the same dims.  out_*: device planes, either all equal to the scene's (in     */
+/* place: only the object's pixels are written) or all distinct from them (a full copy); the  */
+/* object's planes must not overlap them.  mask_out (nullable): [V,H,W] bytes, 1 where the    */
+/* object won.  Asynchronous on `stream`.                                                      */
+/* ---------------------------------------------------------------------------------------- */
+ssgi_status ssgi_composite_gbuffer(const ssgi_gbuffer *scene, const ssgi_gbuffer *object, float *out_depth,
+                                   float *out_normal, float *out_albedo, float *out_rough, float *out_metal,
+                                   uint8_t *mask_out, ssgi_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Depth normals (Sec. 3.1 "depth normal": surface normals from the rendered depth buffer by  */
 /* finite differences, as in 2DGS).  P(x, y) = camera-space point of the pixel centre at its  */
 /* linear depth; per image direction a central difference where both neighbours are          */

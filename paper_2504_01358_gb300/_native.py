@@ -104,6 +104,7 @@ _SIGS = {
     "ssgi_step_fused_phase_ns": (C.c_int, [VP, C.POINTER(C.c_uint64)]),
     "ssgi_read_bandwidth_probe": (C.c_int, [VP, SZ, I32, VP, VP]),
     "ssgi_depth_normals": (C.c_int, [VP, Dims, C.POINTER(Camera), VP, VP]),
+    "ssgi_composite_gbuffer": (C.c_int, [C.POINTER(GBuffer), C.POINTER(GBuffer), VP, VP, VP, VP, VP, VP, VP]),
     "ssgi_serve_create": (C.c_int, [C.POINTER(ServeConfig), C.POINTER(VP)]),
     "ssgi_serve_scene_add": (C.c_int, [VP, Dims, VP, VP, VP, VP, VP, VP, I32, C.POINTER(I64)]),
     "ssgi_serve_scene_remove": (C.c_int, [VP, I64]),

@@ -290,6 +290,19 @@ def ssgi_step_fused_phase_ns(workspace: torch.Tensor) -> dict:
     return dict(zip(FUSED_PHASES, (int(x) for x in a)))
 
 
+def ssgi_composite_gbuffer(scene: GBuffer, obj: GBuffer, out: Optional[GBuffer] = None, mask: bool = False,
+                           stream=None):
+    """Object insertion: merge `obj` into `scene` by depth (in place when `out` is None or `scene`).
+    Returns (out G-buffer, mask [V,H,W] uint8 or None)."""
+    out = scene if out is None else out
+    m = torch.empty(scene.dims, device=scene.depth.device, dtype=torch.uint8) if mask else None
+    gs, go = scene.c_struct(), obj.c_struct()
+    N.call("ssgi_composite_gbuffer", C.byref(gs), C.byref(go), _dev(out.depth, "depth"), _dev(out.normal, "normal"),
+           _dev(out.albedo, "albedo"), _dev(out.rough, "rough"), _dev(out.metal, "metal"),
+           _dev(m, "mask", torch.uint8), _stream(stream))
+    return out, m
+
+
 def ssgi_depth_normals(depth: torch.Tensor, cams, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     """World-space normals [V,H,W,3] from a depth buffer [V,H,W] by finite differences."""
     V, H, W = depth.shape

@@ -124,3 +124,17 @@ def test_depth_normals_rejects_bad_arguments(N):
     assert L.ssgi_depth_normals(fake, N.Dims(1, 8, 8), cams, None, None) == 1
     assert L.ssgi_depth_normals(fake, N.Dims(0, 8, 8), cams, fake, None) == 1
     assert L.ssgi_depth_normals(fake, N.Dims(1, 8, 8), None, fake, None) == 1
+
+
+def test_composite_rejects_bad_arguments(N):
+    L = N.lib()
+    f = [C.c_void_p(0x100000 + 0x1000 * i) for i in range(10)]
+    sc = N.GBuffer(f[0], f[1], f[2], f[3], f[4], N.Dims(1, 8, 8))
+    ob = N.GBuffer(f[5], f[6], f[7], f[8], f[9], N.Dims(1, 8, 8))
+    bad = N.GBuffer(f[5], f[6], f[7], f[8], f[9], N.Dims(1, 8, 9))
+    o = [C.c_void_p(0x900000 + 0x1000 * i) for i in range(5)]
+    assert L.ssgi_composite_gbuffer(C.byref(sc), C.byref(bad), *o, None, None) == 1        # dims differ
+    assert L.ssgi_composite_gbuffer(None, C.byref(ob), *o, None, None) == 1
+    assert L.ssgi_composite_gbuffer(C.byref(sc), C.byref(ob), None, *o[1:], None, None) == 1
+    mixed = [f[0], o[1], o[2], o[3], o[4]]                                                   # partly in place
+    assert L.ssgi_composite_gbuffer(C.byref(sc), C.byref(ob), *mixed, None, None) == 1
