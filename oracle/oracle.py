@@ -16,7 +16,8 @@ import numpy as np
 __all__ = [
     "build", "lib", "philox4x32_10", "ggx_D", "ggx_G1", "fresnel", "ggx_sample_h", "env_levels",
     "build_env_mips", "env_lookup", "build_lut", "lut_sample", "hiz_floats_per_view", "build_hiz",
-    "shade_direct", "depth_normals", "composite_gbuffer", "GBUFFER_KEYS", "trace", "replay_final", "backward", "set_threads", "set_pathwise_step", "max_threads", "FLAG_DIFFUSE_INDIRECT",
+    "shade_direct", "depth_normals", "composite_gbuffer", "GBUFFER_KEYS", "srgb_oetf", "tonemap_srgb",
+    "tonemap_srgb_grad", "l2_loss_srgb", "keyframe_of", "keyframe_lerp", "trace", "replay_final", "backward", "set_threads", "set_pathwise_step", "max_threads", "FLAG_DIFFUSE_INDIRECT",
     "FLAG_BRUTE_FORCE", "FLAG_PATHWISE", "MISS", "INVALID", "BACKGROUND", "forward", "hiz_levels_split", "LUT_N", "LUT_SAMPLES",
 ]
 
@@ -268,6 +269,46 @@ def backward(depth, normal, albedo, rough, metal, cams, mips, He, We, lut, c1, h
     if rc != 0:
         raise ValueError("orc_backward rejected its arguments")
     return {"albedo": ga, "rough": gr, "metal": gm, "normal": gn, "env": ge}
+
+
+# ---- output transform and keyframe lighting (Sec. 3.3 composite sentence; Sec. 4 implementation) ----
+def srgb_oetf(x):
+    """The sRGB transfer function (IEC 61966-2-1) on [0, 1]: 12.92 x up to 0.0031308, then
+    1.055 x^(1/2.4) - 0.055."""
+    x = np.asarray(x, np.float64)
+    return np.where(x <= 0.0031308, 12.92 * x, 1.055 * np.power(np.maximum(x, 0.0031308), 1.0 / 2.4) - 0.055)
+
+
+def tonemap_srgb(linear):
+    """Tone mapping and gamma correction to sRGB after the composite: clamp to [0, 1], then the
+    sRGB transfer function."""
+    return srgb_oetf(np.clip(np.asarray(linear, np.float64), 0.0, 1.0))
+
+
+def tonemap_srgb_grad(linear):
+    """d tonemap_srgb / d linear: 0 outside [0, 1], the transfer function's slope inside."""
+    x = np.asarray(linear, np.float64)
+    inside = (x >= 0.0) & (x <= 1.0)
+    slope = np.where(x <= 0.0031308, 12.92, 1.055 / 2.4 * np.power(np.maximum(x, 0.0031308), 1.0 / 2.4 - 1.0))
+    return np.where(inside, slope, 0.0)
+
+
+def l2_loss_srgb(final, target):
+    """loss = mean((tonemap_srgb(final) - target)^2) and its gradient with respect to final."""
+    f = np.asarray(final, np.float64)
+    r = tonemap_srgb(f) - np.asarray(target, np.float64)
+    return float(np.mean(r * r)), 2.0 * r * tonemap_srgb_grad(f) / r.size
+
+
+def keyframe_of(frame: int, period: int = 10):
+    """Sec. 4 (implementation): every `period`-th frame is a keyframe with its own environment
+    map; a frame in between linearly interpolates its two neighbouring keyframes.  Returns
+    (k, alpha): env(frame) = (1 - alpha) env_k + alpha env_{k+1}."""
+    return frame // period, (frame % period) / period
+
+
+def keyframe_lerp(env_a, env_b, alpha: float):
+    return (1.0 - alpha) * np.asarray(env_a, np.float64) + alpha * np.asarray(env_b, np.float64)
 
 
 GBUFFER_KEYS = ("depth", "normal", "albedo", "rough", "metal")
