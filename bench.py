@@ -598,6 +598,29 @@ def run_ours(args):
                                         "L2 flushed before each of 10 timed calls"}
     del obj, cout
 
+    # output transform of the same frame (Sec. 3.3): sRGB tone map (12 B in + 12 B out per pixel)
+    # and the sRGB L2 loss with its gradient (24 B in + 12 B out per pixel)
+    def epilogue_ms(fn):
+        ts = []
+        for k in range(13):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.mean(ts[3:])
+
+    srgb = torch.empty_like(pipe.final)
+    gfs = torch.empty_like(pipe.final)
+    tm_ms = epilogue_ms(lambda: S.ssgi_tonemap_srgb(pipe.final, out=srgb))
+    ls_ms = epilogue_ms(lambda: S.ssgi_l2_loss_srgb(pipe.final, pipe.target, g_final=gfs, loss=pipe.loss))
+    output_transform = {"tonemap_ms": tm_ms, "tonemap_gbs": 24 * V * H * W / (tm_ms / 1e3) / 1e9,
+                        "srgb_loss_ms": ls_ms, "srgb_loss_gbs": 36 * V * H * W / (ls_ms / 1e3) / 1e9,
+                        "note": "ssgi_tonemap_srgb and ssgi_l2_loss_srgb at the step's frame, L2 flushed"}
+    del srgb, gfs
+
     # march iterations of one trace launch (counted by the kernel itself, untimed)
     counter = torch.zeros(1, device="cuda", dtype=torch.int64)
     pipe.trace(step_count=counter)
@@ -688,6 +711,7 @@ def run_ours(args):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "bandwidth_probe": bw, "adjoint_modes": adjoints,
                 "depth_normals": depth_normals, "object_insertion": composite,
+                "output_transform": output_transform,
                 "fused_step": fused,
                 "serving": serving}
         print(json.dumps(line), flush=True)

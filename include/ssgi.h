@@ -78,6 +78,7 @@ typedef enum {
 #define SSGI_DIFFUSE_INDIRECT 1u /* also estimate diffuse indirect light from the same rays and add it to final */
 #define SSGI_BRUTE_FORCE 2u      /* ignore the pyramid: walk every pixel, no step budget (reference mode) */
 #define SSGI_PATHWISE 4u         /* backward only: pathwise gradients through the sampled directions */
+#define SSGI_SRGB_LOSS 8u        /* fused step only: the L2 loss compares the sRGB image (ssgi_l2_loss_srgb) */
 
 typedef struct { int32_t views, height, width; } ssgi_dims;
 
@@ -110,7 +111,7 @@ typedef struct {
   float thickness;    /* a hit needs the ray to pass behind the depth buffer by at most this (world units) */
   float max_distance; /* ray length in world units (> 0) */
   uint64_t seed;      /* RNG key */
-  uint32_t flags;     /* SSGI_DIFFUSE_INDIRECT | SSGI_BRUTE_FORCE | SSGI_PATHWISE */
+  uint32_t flags;     /* SSGI_DIFFUSE_INDIRECT | SSGI_BRUTE_FORCE | SSGI_PATHWISE | SSGI_SRGB_LOSS */
 } ssgi_trace_params;
 
 /* ---------------------------------------------------------------------------------------- */
@@ -338,6 +339,31 @@ ssgi_status ssgi_backward_noalloc(const float *g_final, const ssgi_gbuffer *g, c
                                   const int32_t *hit_idx, const ssgi_trace_params *p, float *g_albedo,
                                   float *g_rough, float *g_metal, float *g_normal, float *g_env,
                                   ssgi_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Output transform and keyframe lighting.                                                    */
+/* Tone mapping + gamma to sRGB after the composite (Sec. 3.3; the paper names no operator):  */
+/* clamp to [0, 1], then the sRGB transfer function of IEC 61966-2-1 (12.92 x up to 0.0031308, */
+/* 1.055 x^(1/2.4) - 0.055 above).  Keyframe lighting (Sec. 4 implementation details): every   */
+/* period-th frame (10 in the paper) has its own environment map, frames in between blend the */
+/* two neighbouring keyframes linearly.  Arrays are device memory; all calls but               */
+/* ssgi_keyframe_of are asynchronous on `stream`.                                              */
+/* ---------------------------------------------------------------------------------------- */
+/* srgb[i] = T(linear[i]) for n floats (may be the same array). */
+ssgi_status ssgi_tonemap_srgb(const float *linear, float *srgb, int64_t n, ssgi_stream_t stream);
+/* loss = mean((T(final) - target)^2) over n floats against an sRGB target, g_final = its gradient
+ * with respect to the linear final (0 where final is clamped).  loss_out may be NULL. */
+ssgi_status ssgi_l2_loss_srgb(const float *final_in, const float *target, int64_t n, float *g_final, float *loss_out,
+                              ssgi_stream_t stream);
+/* env_out = (1 - alpha) env_a + alpha env_b, maps [env_h][env_w][3], alpha in [0, 1]. */
+ssgi_status ssgi_env_keyframe_lerp(const float *env_a, const float *env_b, float alpha, int32_t env_h, int32_t env_w,
+                                   float *env_out, ssgi_stream_t stream);
+/* Adjoint: g_a = (1 - alpha) g_env, g_b = alpha g_env (added to g_a, g_b when accumulate != 0,
+ * so that gradients of many frames collect in the keyframes); g_a and g_b distinct. */
+ssgi_status ssgi_env_keyframe_lerp_backward(const float *g_env, float alpha, int32_t env_h, int32_t env_w, float *g_a,
+                                            float *g_b, int32_t accumulate, ssgi_stream_t stream);
+/* Host: frame -> (keyframe k, alpha) with env(frame) = (1 - alpha) env_k + alpha env_{k+1}. */
+ssgi_status ssgi_keyframe_of(int64_t frame, int32_t period, int64_t *keyframe, float *alpha);
 
 /* ---------------------------------------------------------------------------------------- */
 /* Object insertion (Sec. 4 "Object Insertion"): an object's G-buffer, rendered on its own,   */

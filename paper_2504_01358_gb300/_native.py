@@ -18,6 +18,7 @@ HIT_MISS, HIT_INVALID, HIT_BACKGROUND = -1, -2, -3
 DIFFUSE_INDIRECT = 1
 BRUTE_FORCE = 2
 PATHWISE = 4
+SRGB_LOSS = 8
 
 STATUS = {
     0: "SSGI_OK", 1: "SSGI_ERR_INVALID_ARG", 2: "SSGI_ERR_UNSUPPORTED", 3: "SSGI_ERR_CUDA", 4: "SSGI_ERR_OOM",
@@ -104,6 +105,11 @@ _SIGS = {
     "ssgi_step_fused_phase_ns": (C.c_int, [VP, C.POINTER(C.c_uint64)]),
     "ssgi_read_bandwidth_probe": (C.c_int, [VP, SZ, I32, VP, VP]),
     "ssgi_depth_normals": (C.c_int, [VP, Dims, C.POINTER(Camera), VP, VP]),
+    "ssgi_tonemap_srgb": (C.c_int, [VP, VP, I64, VP]),
+    "ssgi_l2_loss_srgb": (C.c_int, [VP, VP, I64, VP, VP, VP]),
+    "ssgi_env_keyframe_lerp": (C.c_int, [VP, VP, C.c_float, I32, I32, VP, VP]),
+    "ssgi_env_keyframe_lerp_backward": (C.c_int, [VP, C.c_float, I32, I32, VP, VP, I32, VP]),
+    "ssgi_keyframe_of": (C.c_int, [I64, I32, C.POINTER(I64), C.POINTER(C.c_float)]),
     "ssgi_composite_gbuffer": (C.c_int, [C.POINTER(GBuffer), C.POINTER(GBuffer), VP, VP, VP, VP, VP, VP, VP]),
     "ssgi_serve_create": (C.c_int, [C.POINTER(ServeConfig), C.POINTER(VP)]),
     "ssgi_serve_scene_add": (C.c_int, [VP, Dims, VP, VP, VP, VP, VP, VP, I32, C.POINTER(I64)]),

@@ -46,8 +46,8 @@ __global__ void k_bwd_env(EnvInfo e, const float* __restrict__ g_mips, float* __
 }
 
 __global__ void __launch_bounds__(256) k_l2(const float* __restrict__ f, const float* __restrict__ t, long long n,
-                                            float* __restrict__ g, float* __restrict__ loss) {
-  l2_block(f, t, n, g, loss, (long long)blockIdx.x * blockDim.x, (long long)gridDim.x * blockDim.x);
+                                            float* __restrict__ g, float* __restrict__ loss, bool vec4) {
+  l2_block_vec<false>(f, t, n, g, loss, vec4);
 }
 
 }  // namespace ssgi
@@ -62,7 +62,8 @@ ssgi_status ssgi_l2_loss(const float* final_in, const float* target, int64_t n, 
   cudaStream_t s = (cudaStream_t)stream;
   if (loss_out && cudaMemsetAsync(loss_out, 0, sizeof(float), s) != cudaSuccess) return SSGI_ERR_CUDA;
   const int blocks = (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8);
-  k_l2<<<blocks, 256, 0, s>>>(final_in, target, n, g_final, loss_out);
+  const bool vec4 = (((uintptr_t)final_in | (uintptr_t)target | (uintptr_t)g_final) & 15) == 0;
+  k_l2<<<blocks, 256, 0, s>>>(final_in, target, n, g_final, loss_out, vec4);
   return launch_status();
 }
 

@@ -186,7 +186,8 @@ __global__ void __launch_bounds__(kFusedThreads, 8) k_step_fused(const __grid_co
       const int x = (r % tx) * 8 + (threadIdx.x % 8), y = (r / tx) * 16 + (threadIdx.x / 8);
       if (x < W && y < H) {
         const float3 fin = trace_pixel<kCid>(A, x, y, v, s_hoff, s_hw);
-        acc += l2_pixel(A, v * HW + (long long)y * W + x, fin, inv);
+        const long long p = v * HW + (long long)y * W + x;
+        acc += (A.flags & SSGI_SRGB_LOSS) ? l2_srgb_pixel(A, p, fin, inv) : l2_pixel(A, p, fin, inv);
       }
     });
     block_sum_add(acc, F.loss, inv);

@@ -704,26 +704,73 @@ __device__ __forceinline__ void block_sum_add(float acc, float* out, float scale
   __syncthreads();
 }
 
-// Block-level (blockDim <= 256): g = d/df of mean((f - t)^2) over n floats, loss += the mean.
-__device__ __forceinline__ void l2_block(const float* __restrict__ f, const float* __restrict__ t, long long n,
-                                         float* __restrict__ g, float* __restrict__ loss, long long start,
-                                         long long stride) {
-  const float inv = 1.0f / (float)n;
-  float acc = 0.0f;
-  for (long long i = start + threadIdx.x; i < n; i += stride) {
-    const float r = __ldg(f + i) - __ldg(t + i);
-    g[i] = 2.0f * r * inv;
-    acc += r * r;
-  }
-  if (!loss) return;  // block-uniform
-  block_sum_add(acc, loss, inv);
-}
-
-// The same loss term for one pixel's final colour (already in registers); returns |r|^2.
+// The L2 loss term of one pixel's final colour (already in registers); returns |r|^2.
 __device__ __forceinline__ float l2_pixel(const FrameArgs& A, long long p, float3 fin, float inv) {
   const float3 t = ld3(A.target + 3 * p);
   const float rx = fin.x - t.x, ry = fin.y - t.y, rz = fin.z - t.z;
   st3(A.g_final + 3 * p, f3(2.0f * rx * inv, 2.0f * ry * inv, 2.0f * rz * inv));
+  return rx * rx + ry * ry + rz * rz;
+}
+
+// ==========================================================================================
+// Output transform: tone mapping + gamma to sRGB after the composite (Sec. 3.3): clamp to
+// [0, 1], then the sRGB transfer function (IEC 61966-2-1).
+// ==========================================================================================
+__device__ __forceinline__ float tonemap_srgb(float x) {
+  x = fminf(fmaxf(x, 0.0f), 1.0f);
+  return x <= 0.0031308f ? 12.92f * x : fmaf(1.055f, powf(x, 1.0f / 2.4f), -0.055f);
+}
+
+// d tonemap_srgb / dx: 0 outside [0, 1].
+__device__ __forceinline__ float tonemap_srgb_slope(float x) {
+  if (!(x >= 0.0f && x <= 1.0f)) return 0.0f;
+  return x <= 0.0031308f ? 12.92f : (1.055f / 2.4f) * powf(x, 1.0f / 2.4f - 1.0f);
+}
+
+// One element of the L2 loss: writes g and returns r^2 (kSrgb: against T(f), T = tonemap_srgb).
+template <bool kSrgb>
+__device__ __forceinline__ float l2_elem(float f, float t, float inv, float& g) {
+  if (kSrgb) {
+    const float r = tonemap_srgb(f) - t;
+    g = 2.0f * r * tonemap_srgb_slope(f) * inv;
+    return r * r;
+  }
+  const float r = f - t;
+  g = 2.0f * r * inv;
+  return r * r;
+}
+
+// Block-level (blockDim <= 256) L2 loss over n floats with 16-byte accesses (f, t and g
+// 16-byte aligned when vec4 is set), the ragged tail element by element: g = d/df of the mean,
+// loss += the mean.
+template <bool kSrgb>
+__device__ __forceinline__ void l2_block_vec(const float* __restrict__ f, const float* __restrict__ t, long long n,
+                                             float* __restrict__ g, float* __restrict__ loss, bool vec4) {
+  const float inv = 1.0f / (float)n;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n4 = vec4 ? n / 4 : 0;
+  float acc = 0.0f;
+  for (long long i = t0; i < n4; i += stride) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(f) + i), b = __ldg(reinterpret_cast<const float4*>(t) + i);
+    float4 o;
+    acc += l2_elem<kSrgb>(a.x, b.x, inv, o.x);
+    acc += l2_elem<kSrgb>(a.y, b.y, inv, o.y);
+    acc += l2_elem<kSrgb>(a.z, b.z, inv, o.z);
+    acc += l2_elem<kSrgb>(a.w, b.w, inv, o.w);
+    reinterpret_cast<float4*>(g)[i] = o;
+  }
+  for (long long i = 4 * n4 + t0; i < n; i += stride) acc += l2_elem<kSrgb>(__ldg(f + i), __ldg(t + i), inv, g[i]);
+  if (!loss) return;  // block-uniform
+  block_sum_add(acc, loss, inv);
+}
+
+// The sRGB loss term of one pixel's final colour in registers; returns |r|^2.
+__device__ __forceinline__ float l2_srgb_pixel(const FrameArgs& A, long long p, float3 fin, float inv) {
+  const float3 t = ld3(A.target + 3 * p);
+  const float rx = tonemap_srgb(fin.x) - t.x, ry = tonemap_srgb(fin.y) - t.y, rz = tonemap_srgb(fin.z) - t.z;
+  st3(A.g_final + 3 * p, f3(2.0f * rx * tonemap_srgb_slope(fin.x) * inv, 2.0f * ry * tonemap_srgb_slope(fin.y) * inv,
+                            2.0f * rz * tonemap_srgb_slope(fin.z) * inv));
   return rx * rx + ry * ry + rz * rz;
 }
 

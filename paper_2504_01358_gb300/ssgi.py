@@ -290,6 +290,46 @@ def ssgi_step_fused_phase_ns(workspace: torch.Tensor) -> dict:
     return dict(zip(FUSED_PHASES, (int(x) for x in a)))
 
 
+def ssgi_tonemap_srgb(linear: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """sRGB image: clamp to [0, 1], then the sRGB transfer function (tone mapping + gamma)."""
+    out = torch.empty_like(linear) if out is None else out
+    N.call("ssgi_tonemap_srgb", _dev(linear, "linear"), _dev(out, "srgb"), linear.numel(), _stream(stream))
+    return out
+
+
+def ssgi_l2_loss_srgb(final: torch.Tensor, target: torch.Tensor, g_final=None, loss=None, stream=None):
+    """loss = mean((tonemap_srgb(final) - target)^2) and its gradient with respect to final."""
+    g_final = torch.empty_like(final) if g_final is None else g_final
+    loss = torch.empty(1, device=final.device, dtype=torch.float32) if loss is None else loss
+    N.call("ssgi_l2_loss_srgb", _dev(final, "final"), _dev(target, "target"), final.numel(),
+           _dev(g_final, "g_final"), _dev(loss, "loss"), _stream(stream))
+    return g_final, loss
+
+
+def ssgi_env_keyframe_lerp(env_a: torch.Tensor, env_b: torch.Tensor, alpha: float,
+                           out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """(1 - alpha) env_a + alpha env_b for two [h, w, 3] keyframe maps."""
+    h, w = int(env_a.shape[0]), int(env_a.shape[1])
+    out = torch.empty_like(env_a) if out is None else out
+    N.call("ssgi_env_keyframe_lerp", _dev(env_a, "env_a"), _dev(env_b, "env_b"), float(alpha), h, w,
+           _dev(out, "env_out"), _stream(stream))
+    return out
+
+
+def ssgi_env_keyframe_lerp_backward(g_env: torch.Tensor, alpha: float, g_a: torch.Tensor, g_b: torch.Tensor,
+                                    accumulate: bool = True, stream=None) -> None:
+    h, w = int(g_env.shape[0]), int(g_env.shape[1])
+    N.call("ssgi_env_keyframe_lerp_backward", _dev(g_env, "g_env"), float(alpha), h, w, _dev(g_a, "g_a"),
+           _dev(g_b, "g_b"), 1 if accumulate else 0, _stream(stream))
+
+
+def ssgi_keyframe_of(frame: int, period: int = 10):
+    """(keyframe k, alpha): env(frame) = (1 - alpha) env_k + alpha env_{k+1}."""
+    k, a = C.c_int64(), C.c_float()
+    N.call("ssgi_keyframe_of", int(frame), int(period), C.byref(k), C.byref(a))
+    return int(k.value), float(a.value)
+
+
 def ssgi_composite_gbuffer(scene: GBuffer, obj: GBuffer, out: Optional[GBuffer] = None, mask: bool = False,
                            stream=None):
     """Object insertion: merge `obj` into `scene` by depth (in place when `out` is None or `scene`).
@@ -412,7 +452,8 @@ class FramePipeline:
                             hit_idx=self.hit_idx, step_count=step_count, stream=stream)
 
     def loss_grad(self, stream=None) -> None:
-        ssgi_l2_loss(self.final, self.target, g_final=self.g_final, loss=self.loss, stream=stream)
+        loss = ssgi_l2_loss_srgb if self.params.flags & N.SRGB_LOSS else ssgi_l2_loss
+        loss(self.final, self.target, g_final=self.g_final, loss=self.loss, stream=stream)
 
     def adjoint(self, stream=None) -> None:
         ssgi_backward(self.g_final, self.g, self.cam, self.c1, self.em, self.lut, self.hit_idx, self.params,

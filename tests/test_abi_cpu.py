@@ -138,3 +138,21 @@ def test_composite_rejects_bad_arguments(N):
     assert L.ssgi_composite_gbuffer(C.byref(sc), C.byref(ob), None, *o[1:], None, None) == 1
     mixed = [f[0], o[1], o[2], o[3], o[4]]                                                   # partly in place
     assert L.ssgi_composite_gbuffer(C.byref(sc), C.byref(ob), *mixed, None, None) == 1
+
+
+def test_keyframe_of_matches_the_oracle_and_rejects_bad_arguments(N):
+    L = N.lib()
+    k, a = C.c_int64(), C.c_float()
+    for frame in (0, 1, 9, 10, 11, 27, 99, 100, 12345):
+        for period in (1, 3, 10):
+            assert L.ssgi_keyframe_of(frame, period, C.byref(k), C.byref(a)) == 0
+            ko, ao = O.keyframe_of(frame, period)
+            assert k.value == ko and abs(a.value - ao) <= 1e-7
+    assert L.ssgi_keyframe_of(-1, 10, C.byref(k), C.byref(a)) == 1
+    assert L.ssgi_keyframe_of(5, 0, C.byref(k), C.byref(a)) == 1
+    fake = C.c_void_p(0x100000)
+    assert L.ssgi_tonemap_srgb(fake, None, 16, None) == 1
+    assert L.ssgi_tonemap_srgb(fake, fake, 0, None) == 1
+    assert L.ssgi_l2_loss_srgb(fake, fake, 0, fake, None, None) == 1
+    assert L.ssgi_env_keyframe_lerp(fake, fake, C.c_float(1.5), 4, 8, fake, None) == 1
+    assert L.ssgi_env_keyframe_lerp_backward(fake, C.c_float(0.5), 4, 8, fake, fake, 1, None) == 1  # g_a == g_b

@@ -18,7 +18,8 @@ def _per_stage(S, wl, lut):
     hiz = S.ssgi_build_hiz(g.depth, p.hiz_levels) if p.hiz_levels > 1 else None
     c_d, _, c1 = S.ssgi_shade_direct(g, cams, em, lut)
     tr = S.ssgi_trace_indirect(g, cams, hiz, c1, c_d, em, p, want_hits=True)
-    gf, loss = S.ssgi_l2_loss(tr["final"], tgt)
+    lossf = S.ssgi_l2_loss_srgb if p.flags & 8 else S.ssgi_l2_loss
+    gf, loss = lossf(tr["final"], tgt)
     gr = S.ssgi_backward(gf, g, cams, c1, em, lut, tr["hit_idx"], p)
     torch.cuda.synchronize()
     out = {k: v.cpu().numpy() for k, v in gr.items()}
@@ -48,7 +49,7 @@ def _compare(a, b):
         assert float(np.abs(a[k] - b[k]).max()) / scale <= 1e-4, k
 
 
-@pytest.mark.parametrize("flags", [0, 1, 4, 5])
+@pytest.mark.parametrize("flags", [0, 1, 4, 5, 8, 9])
 def test_fused_step_equals_the_per_stage_path(flags):
     import paper_2504_01358_gb300 as S
     scene = si.make_scene(31, 10, 4.0, 1)
