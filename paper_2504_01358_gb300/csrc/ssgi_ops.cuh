@@ -314,22 +314,24 @@ __device__ __forceinline__ int march(const FrameArgs& A, const DevCam& c, const 
     const float se = fminf(sx, sy);
     const float kb = fmaf(fminf(se, 1.0f), r.dk, r.k0);
     const float kmin = fminf(r.ka, kb), kmax = fmaxf(r.ka, kb);
-    const float hzv = (r.L == 0) ? __ldg(dep + r.iy * W + r.ix)
-                                 : __ldg(hz_v + s_hoff[r.L] + (r.iy >> r.L) * s_hw[r.L] + (r.ix >> r.L));
-    if (kmin * hzv > 1.0f) {
-      if (!(se < 1.0f)) return SSGI_HIT_MISS;  // the cell holds the end of the segment
-      step_out(r, sx, sy);
-      r.ka = kb;
-      if (r.L + 1 < levels) ++r.L;
-    } else if (r.L > 0) {
-      --r.L;
-    } else if (kmax * (hzv + thick) >= 1.0f) {
-      return r.iy * W + r.ix;
-    } else {
-      if (!(se < 1.0f)) return SSGI_HIT_MISS;
-      step_out(r, sx, sy);
-      r.ka = kb;
+    // one load for every level (level 0 is the depth buffer itself)
+    const float* base = r.L ? hz_v + s_hoff[r.L] : dep;
+    const int wl = r.L ? s_hw[r.L] : W;
+    const float hzv = __ldg(base + (r.iy >> r.L) * wl + (r.ix >> r.L));
+    const bool skip = kmin * hzv > 1.0f;
+    if (!skip) {
+      if (r.L > 0) {  // something in this cell may be hit: refine
+        --r.L;
+        continue;
+      }
+      if (kmax * (hzv + thick) >= 1.0f) return r.iy * W + r.ix;
     }
+    // leave the cell: skipped at any level, or passed behind a level-0 pixel (one code path for
+    // both, so a warp whose lanes do either runs it once)
+    if (!(se < 1.0f)) return SSGI_HIT_MISS;  // the cell holds the end of the segment
+    step_out(r, sx, sy);
+    r.ka = kb;
+    if (skip && r.L + 1 < levels) ++r.L;
   }
 }
 
