@@ -254,18 +254,21 @@ __device__ __forceinline__ void exits(const Ray& r, float& sx, float& sy) {
 
 // Enter the pixel across the exit side of the level-L cell (ties go to x), on the row (column)
 // of the exit point clamped to the cell.
+// Written with selects instead of a branch on the exit side: lanes of a warp that leave their
+// cells through different sides do not diverge here.
 __device__ __forceinline__ void step_out(Ray& r, float sx, float sy) {
   const int lo_x = (r.ix >> r.L) << r.L, lo_y = (r.iy >> r.L) << r.L;
   const int S1 = (1 << r.L) - 1;
-  if (sx <= sy) {
-    const int fy = __float2int_rd(fmaf(sx, r.Dy, r.P0y));
-    r.iy = min(max(fy, lo_y), lo_y + S1);
-    r.ix = r.sgx ? lo_x + S1 + 1 : lo_x - 1;
-  } else {
-    const int fx = __float2int_rd(fmaf(sy, r.Dx, r.P0x));
-    r.ix = min(max(fx, lo_x), lo_x + S1);
-    r.iy = r.sgy ? lo_y + S1 + 1 : lo_y - 1;
-  }
+  const bool xe = sx <= sy;
+  // the coordinate along the side that is not crossed, at the exit point, clamped to the cell
+  const int f = __float2int_rd(xe ? fmaf(sx, r.Dy, r.P0y) : fmaf(sy, r.Dx, r.P0x));
+  const int lo_o = xe ? lo_y : lo_x;
+  const int along = min(max(f, lo_o), lo_o + S1);
+  // the crossed coordinate: the first pixel beyond the cell
+  const int lo_m = xe ? lo_x : lo_y;
+  const int across = (xe ? r.sgx : r.sgy) ? lo_m + S1 + 1 : lo_m - 1;
+  r.ix = xe ? across : along;
+  r.iy = xe ? along : across;
 }
 
 // March from pixel (x, y) at linear depth z0 (k0 = 1/z0) along camera-space direction w.
