@@ -316,7 +316,7 @@ size_t ssgi_serve_request_bytes(ssgi_dims d, int32_t env_h, int32_t env_w, int32
 /* Allocation-free backward (no counterpart in the paper; an interface convenience)          */
 /* ---------------------------------------------------------------------------------------- */
 /* Largest scratch the allocation-free backward can use: 32 MiB.  That covers one 1600x900
- * view with a 256x512 environment (19.4 MB); see ssgi_backward_workspace_bytes. */
+ * view with a 256x512 environment (25.8 MB); see ssgi_backward_workspace_bytes. */
 #define SSGI_BACKWARD_NOALLOC_MAX_BYTES (32u << 20)
 
 /* Same computation, arguments and outputs as ssgi_backward, for callers that cannot allocate

@@ -145,9 +145,10 @@ size_t ssgi_backward_workspace_bytes(ssgi_dims d, int32_t env_h, int32_t env_w) 
   if (!ssgi::dims_ok(d)) return 0;
   const size_t mf = ssgi_env_mip_floats(env_h, env_w);
   if (mf == 0) return 0;
+  // g_c1: one RGB + pad (16 bytes) per pixel; the mip-chain gradient: one per texel
   const size_t px = (size_t)d.views * d.height * d.width;
-  const size_t a = (px * 3 * sizeof(float) + 255) & ~(size_t)255;
-  return a + ((mf * sizeof(float) + 255) & ~(size_t)255);
+  const size_t a = (px * 16 + 255) & ~(size_t)255;
+  return a + ((mf / 3 * 16 + 255) & ~(size_t)255);
 }
 
 }  // extern "C"

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256) k_bwd_direct(FrameArgs A) {
   bwd_direct_pixel(A, p);
 }
 
-__global__ void k_bwd_env(EnvInfo e, const float* __restrict__ g_mips, float* __restrict__ g_env) {
+__global__ void k_bwd_env(EnvInfo e, const float4* __restrict__ g_mips, float* __restrict__ g_env) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= e.h[0] * e.w[0] * 3) return;
   bwd_env_item(e, g_mips, g_env, t);
@@ -80,9 +80,9 @@ ssgi_status ssgi_backward(const float* g_final, const ssgi_gbuffer* g, const ssg
   const size_t need = ssgi_backward_workspace_bytes(g->d, env->h, env->w);
   if (need == 0 || ws_bytes < need) return SSGI_ERR_INVALID_ARG;
   const long long npx = (long long)g->d.views * g->d.height * g->d.width;
-  const size_t c1_bytes = ((size_t)npx * 3 * sizeof(float) + 255) & ~(size_t)255;
-  A.g_c1 = (float*)workspace;
-  A.g_mips = (float*)((char*)workspace + c1_bytes);
+  const size_t c1_bytes = ((size_t)npx * sizeof(float4) + 255) & ~(size_t)255;
+  A.g_c1 = (float4*)workspace;
+  A.g_mips = (float4*)((char*)workspace + c1_bytes);
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(workspace, 0, need, s) != cudaSuccess) return SSGI_ERR_CUDA;
   A.g_final = const_cast<float*>(g_final);
@@ -164,9 +164,9 @@ extern "C" ssgi_status ssgi_backward_noalloc(const float* g_final, const ssgi_gb
   const ssgi_status ss = noalloc_scratch(&workspace);
   if (ss != SSGI_OK) return ss;
   const long long npx = (long long)g->d.views * g->d.height * g->d.width;
-  const size_t c1_bytes = ((size_t)npx * 3 * sizeof(float) + 255) & ~(size_t)255;
-  A.g_c1 = (float*)workspace;
-  A.g_mips = (float*)((char*)workspace + c1_bytes);
+  const size_t c1_bytes = ((size_t)npx * sizeof(float4) + 255) & ~(size_t)255;
+  A.g_c1 = (float4*)workspace;
+  A.g_mips = (float4*)((char*)workspace + c1_bytes);
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(workspace, 0, need, s) != cudaSuccess) return SSGI_ERR_CUDA;
   A.g_final = const_cast<float*>(g_final);

@@ -47,8 +47,8 @@ struct FusedArgs {
   float* g_env;      // output
   float* loss;       // output (one float)
   unsigned* ctl;     // workspace: control block
-  long long n_gc1;   // floats of g_c1
-  int n_gmips;       // floats of g_mips
+  long long n_gc1;   // float4s of g_c1
+  int n_gmips;       // float4s of g_mips
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -147,8 +147,8 @@ __global__ void __launch_bounds__(kFusedThreads, 8) k_step_fused(const __grid_co
 
   // P0: clear the backward accumulators and the loss; Hi-Z and environment pyramids, 32 x 32
   // tiles through level 5, levels 6.. by the block that finishes a pyramid's last tile.
-  for (long long i = gtid; i < F.n_gc1; i += gsz) A.g_c1[i] = 0.0f;
-  for (long long i = gtid; i < F.n_gmips; i += gsz) A.g_mips[i] = 0.0f;
+  for (long long i = gtid; i < F.n_gc1; i += gsz) A.g_c1[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (long long i = gtid; i < F.n_gmips; i += gsz) A.g_mips[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   if (gtid == 0) *F.loss = 0.0f;
   {
     const int hx = (W + kHizTile - 1) / kHizTile, hy = (H + kHizTile - 1) / kHizTile;
@@ -233,8 +233,8 @@ inline FusedLayout fused_layout(ssgi_dims d, int env_h, int env_w, int levels) {
   L.cd = o; o += up256(px * 12);
   L.c1 = o; o += up256(px * 12);
   L.gfinal = o; o += up256(px * 12);
-  L.gc1 = o; o += up256(px * 12);
-  L.gmips = o; o += up256(ssgi_env_mip_floats(env_h, env_w) * 4);
+  L.gc1 = o; o += up256(px * 16);
+  L.gmips = o; o += up256(ssgi_env_mip_floats(env_h, env_w) / 3 * 16);
   L.bytes = o;
   return L;
 }
@@ -277,8 +277,8 @@ ssgi_status ssgi_step_fused(const ssgi_gbuffer* g, const ssgi_camera* cams, cons
   F.g_env = g_env;
   F.loss = loss;
   F.ctl = (unsigned*)(ws + L.bar);
-  F.n_gc1 = npx * 3;
-  F.n_gmips = (int)ssgi_env_mip_floats(env_h, env_w);
+  F.n_gc1 = npx;
+  F.n_gmips = (int)(ssgi_env_mip_floats(env_h, env_w) / 3);
   A.depth = g->depth;
   A.normal = g->normal;
   A.albedo = g->albedo;
@@ -298,8 +298,8 @@ ssgi_status ssgi_step_fused(const ssgi_gbuffer* g, const ssgi_camera* cams, cons
   A.g_rough = g_rough;
   A.g_metal = g_metal;
   A.g_normal = g_normal;
-  A.g_c1 = (float*)(ws + L.gc1);
-  A.g_mips = (float*)(ws + L.gmips);
+  A.g_c1 = (float4*)(ws + L.gc1);
+  A.g_mips = (float4*)(ws + L.gmips);
   A.spp = p->spp;
   A.max_steps = p->max_steps;
   A.levels = p->hiz_levels;

@@ -37,8 +37,8 @@ struct FrameArgs {
   float* g_rough;
   float* g_metal;
   float* g_normal;
-  float* g_c1;    // backward workspace [V,H,W,3]
-  float* g_mips;  // backward workspace, packed like the mips
+  float4* g_c1;    // backward workspace [V,H,W] RGB + pad: one 16-byte atomic per scatter
+  float4* g_mips;  // backward workspace, one RGB + pad per texel, levels packed like the mips
   int spp, max_steps, levels;
   float thickness, max_distance;
   uint64_t seed;
@@ -412,7 +412,9 @@ __device__ __forceinline__ float3 trace_pixel(const FrameArgs& A, int x, int y, 
 // ==========================================================================================
 // Backward (replay adjoint) and L2 loss
 // ==========================================================================================
-__device__ __forceinline__ void atomic_add3(float* p, float3 v) {
+// Adds v to the RGB of *p (w unused), summing first over the lanes of the warp that add to the
+// same address; one 16-byte vector atomic per distinct address.
+__device__ __forceinline__ void atomic_add4(float4* p, float3 v) {
   const unsigned act = __activemask();
   const unsigned grp = __match_any_sync(act, (unsigned long long)p);
   const int lane = threadIdx.x & 31;
@@ -424,11 +426,7 @@ __device__ __forceinline__ void atomic_add3(float* p, float3 v) {
       v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
       v.z += __shfl_xor_sync(0xffffffffu, v.z, o);
     }
-    if (lane == 0) {
-      atomicAdd(p + 0, v.x);
-      atomicAdd(p + 1, v.y);
-      atomicAdd(p + 2, v.z);
-    }
+    if (lane == 0) atomicAdd(p, make_float4(v.x, v.y, v.z, 0.0f));
     return;
   }
   // lanes sharing an address form a list in lane order; pointer jumping doubles the span of
@@ -444,11 +442,7 @@ __device__ __forceinline__ void atomic_add3(float* p, float3 v) {
       nxt = nn;
     }
   }
-  if (lane == __ffs(grp) - 1) {
-    atomicAdd(p + 0, v.x);
-    atomicAdd(p + 1, v.y);
-    atomicAdd(p + 2, v.z);
-  }
+  if (lane == __ffs(grp) - 1) atomicAdd(p, make_float4(v.x, v.y, v.z, 0.0f));
 }
 
 // d ln G1(z; rho) / dz, / drho
@@ -470,7 +464,7 @@ __device__ __forceinline__ void dlnD(float c, float rho, float& dc, float& dr) {
 // Scatter g (per channel) with weight `scale` through the bilinear taps into gm, and return
 // the derivatives of the bilinear value contracted with g along x and y (texel units).
 __device__ __forceinline__ void bilin_adj(const float* __restrict__ mips, const Taps& t, float3 g, float scale,
-                                          float* gm, float& gx, float& gy) {
+                                          float4* gm, float& gx, float& gy) {
   const float3 a = ld3(mips + t.idx[0]), b = ld3(mips + t.idx[1]);
   const float3 c = ld3(mips + t.idx[2]), d = ld3(mips + t.idx[3]);
   gx = dot3(g, (b - a) * (1.0f - t.ty) + (d - c) * t.ty);
@@ -478,17 +472,18 @@ __device__ __forceinline__ void bilin_adj(const float* __restrict__ mips, const 
   if (scale != 0.0f) {
     const float w00 = (1.0f - t.tx) * (1.0f - t.ty), w01 = t.tx * (1.0f - t.ty);
     const float w10 = (1.0f - t.tx) * t.ty, w11 = t.tx * t.ty;
-    atomic_add3(gm + t.idx[0], g * (scale * w00));
-    atomic_add3(gm + t.idx[1], g * (scale * w01));
-    atomic_add3(gm + t.idx[2], g * (scale * w10));
-    atomic_add3(gm + t.idx[3], g * (scale * w11));
+    // tap offsets count floats of the packed RGB chain (3 per texel); gm holds one float4 per texel
+    atomic_add4(gm + t.idx[0] / 3, g * (scale * w00));
+    atomic_add4(gm + t.idx[1] / 3, g * (scale * w01));
+    atomic_add4(gm + t.idx[2] / 3, g * (scale * w10));
+    atomic_add4(gm + t.idx[3] / 3, g * (scale * w11));
   }
 }
 
 // Adjoint of SampleEnvMap(d, lambda): texel gradients into gm (all levels), returns d/dd and
 // d/dlambda (zero where lambda is clamped).
 __device__ __forceinline__ float3 env_lookup_adj(const float* __restrict__ mips, const EnvInfo& e, float3 d,
-                                                 float lam, float3 g, float* gm, float& glam) {
+                                                 float lam, float3 g, float4* gm, float& glam) {
   const float lmax = (float)(e.levels - 1);
   const bool inside = lam > 0.0f && lam < lmax;
   lam = fminf(fmaxf(lam, 0.0f), lmax);
@@ -590,7 +585,7 @@ __device__ __forceinline__ void bwd_mc_pixel(const FrameArgs& A, long long p) {
       }
       float3 gdir = f3(0.f, 0.f, 0.f);  // d loss / d w through a miss's lookup
       if (q >= 0) {
-        atomic_add3(A.g_c1 + 3 * (view * HW + q), gL);
+        atomic_add4(A.g_c1 + (view * HW + q), gL);
       } else if (kPathwise) {
         float glam;
         gdir = env_lookup_adj(A.mips, A.e, sm.w, 0.0f, gL, A.g_mips, glam);
@@ -638,7 +633,8 @@ __device__ __forceinline__ void bwd_direct_pixel(const FrameArgs& A, long long p
   const int y = rem / A.vs.W, x = rem - y * A.vs.W;
   const DevCam& cam = A.vs.cam[view];
   const float3 d = pix_dir_world(cam, x, y);
-  const float3 gc1 = ld3(A.g_c1 + 3 * p);
+  const float4 gq = __ldcg(A.g_c1 + p);  // written by atomics earlier: read through L2
+  const float3 gc1 = f3(gq.x, gq.y, gq.z);
   const float3 gcd = ld3(A.g_final + 3 * p) + gc1;
   const float3 gcs = gc1;
   const float z = __ldg(A.depth + p);
@@ -682,13 +678,15 @@ __device__ __forceinline__ void bwd_direct_pixel(const FrameArgs& A, long long p
   A.g_metal[p] += gm;
 }
 
-__device__ __forceinline__ void bwd_env_item(const EnvInfo& e, const float* __restrict__ g_mips,
+__device__ __forceinline__ void bwd_env_item(const EnvInfo& e, const float4* __restrict__ g_mips,
                                              float* __restrict__ g_env, int t) {
   const int w0 = e.w[0];
   const int c = t % 3, j = (t / 3) % w0, i = t / (3 * w0);
+  const float* gm = reinterpret_cast<const float*>(g_mips);
   float acc = 0.0f, scale = 1.0f;
   for (int l = 0; l < e.levels; ++l) {
-    acc += scale * __ldg(g_mips + e.off[l] + ((i >> l) * e.w[l] + (j >> l)) * 3 + c);
+    // texel (i >> l, j >> l) of level l; e.off counts floats of the packed RGB chain
+    acc += scale * __ldcg(gm + 4 * (e.off[l] / 3 + (i >> l) * e.w[l] + (j >> l)) + c);
     scale *= 0.25f;
   }
   g_env[t] = acc;
