@@ -131,12 +131,8 @@ __device__ __forceinline__ bool grid_sync(unsigned* ctl) {
 template <bool kCid, bool kPathwise>
 __global__ void __launch_bounds__(kFusedThreads, 8) k_step_fused(const __grid_constant__ FusedArgs F) {
   const FrameArgs& A = F.f;
-  __shared__ int s_hoff[SSGI_MAX_HIZ_LEVELS], s_hw[SSGI_MAX_HIZ_LEVELS];
+  __shared__ LevelTable s_lv;
   __shared__ TileBuf s_tile;
-  if (threadIdx.x < SSGI_MAX_HIZ_LEVELS) {
-    s_hoff[threadIdx.x] = A.hz.off[threadIdx.x];
-    s_hw[threadIdx.x] = A.hz.w[threadIdx.x];
-  }
   const int V = A.vs.V, H = A.vs.H, W = A.vs.W;
   const long long HW = (long long)H * W, npx = V * HW;
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -184,8 +180,10 @@ __global__ void __launch_bounds__(kFusedThreads, 8) k_step_fused(const __grid_co
     for_each_chunk(ctl + kTraceNext, tx * ty * V, [&](int t) {
       const int v = t / (tx * ty), r = t - v * tx * ty;
       const int x = (r % tx) * 8 + (threadIdx.x % 8), y = (r / tx) * 16 + (threadIdx.x / 8);
+      fill_levels(A, v, s_lv);  // the previous tile's reads ended at for_each_chunk's barriers
+      __syncthreads();
       if (x < W && y < H) {
-        const float3 fin = trace_pixel<kCid>(A, x, y, v, s_hoff, s_hw);
+        const float3 fin = trace_pixel<kCid>(A, x, y, v, s_lv);
         const long long p = v * HW + (long long)y * W + x;
         acc += (A.flags & SSGI_SRGB_LOSS) ? l2_srgb_pixel(A, p, fin, inv) : l2_pixel(A, p, fin, inv);
       }

@@ -27,16 +27,13 @@ constexpr int kTileH = 16;  // a 128-thread block covers 8 x 16 pixels
 // rays start close together and touch the same pyramid cells.
 template <bool kCid>
 __global__ void __launch_bounds__(kTileW * kTileH, 8) k_trace(FrameArgs A) {
-  __shared__ int s_hoff[SSGI_MAX_HIZ_LEVELS], s_hw[SSGI_MAX_HIZ_LEVELS];
-  if (threadIdx.x < SSGI_MAX_HIZ_LEVELS) {
-    s_hoff[threadIdx.x] = A.hz.off[threadIdx.x];
-    s_hw[threadIdx.x] = A.hz.w[threadIdx.x];
-  }
+  __shared__ LevelTable s_lv;
+  fill_levels(A, blockIdx.z, s_lv);
   __syncthreads();
   const int x = blockIdx.x * kTileW + (threadIdx.x % kTileW);
   const int y = blockIdx.y * kTileH + (threadIdx.x / kTileW);
   if (x >= A.vs.W || y >= A.vs.H) return;
-  trace_pixel<kCid>(A, x, y, blockIdx.z, s_hoff, s_hw);
+  trace_pixel<kCid>(A, x, y, blockIdx.z, s_lv);
 }
 
 }  // namespace ssgi

@@ -234,6 +234,25 @@ __device__ __forceinline__ void shade_pixel(const FrameArgs& A, long long p) {
 // ==========================================================================================
 // Trace (Sec. 3.3, Appendix D)
 // ==========================================================================================
+// Per-level base pointer and row width of the pyramid of one view, level 0 being the depth
+// buffer itself, so that the march reads every level through the same code (shared memory,
+// filled by the block for the view it traces).
+struct LevelTable {
+  const float* base[SSGI_MAX_HIZ_LEVELS];
+  int w[SSGI_MAX_HIZ_LEVELS];
+};
+
+// Block-level part: threads 0..SSGI_MAX_HIZ_LEVELS-1 fill the table; the caller synchronises.
+__device__ __forceinline__ void fill_levels(const FrameArgs& A, int view, LevelTable& t) {
+  const int l = threadIdx.x;
+  if (l < SSGI_MAX_HIZ_LEVELS) {
+    const long long HW = (long long)A.vs.H * A.vs.W;
+    t.base[l] = l == 0 ? A.depth + view * HW
+                       : (A.hiz && l < A.hz.levels ? A.hiz + (long long)view * A.hz.per_view + A.hz.off[l] : nullptr);
+    t.w[l] = l == 0 ? A.vs.W : A.hz.w[l];
+  }
+}
+
 // One ray's march state.  The segment constants give the exit parameter of a cell edge bx as
 // s_x = bx * iDx + ox (iDx = 0, ox = +inf when the segment has no x extent).  Depth is handled
 // as k = 1/z, which is linear in the screen parameter, and the tests are written on k:
@@ -273,9 +292,8 @@ __device__ __forceinline__ void step_out(Ray& r, float sx, float sy) {
 
 // March from pixel (x, y) at linear depth z0 (k0 = 1/z0) along camera-space direction w.
 // Returns the hit pixel's index within the view, or SSGI_HIT_MISS; `it` gets the iterations.
-__device__ __forceinline__ int march(const FrameArgs& A, const DevCam& c, const float* __restrict__ dep,
-                                     const float* __restrict__ hz_v, const int* __restrict__ s_hoff,
-                                     const int* __restrict__ s_hw, int levels, int max_steps, int x, int y,
+__device__ __forceinline__ int march(const FrameArgs& A, const DevCam& c, const LevelTable& lt, int levels,
+                                     int max_steps, int x, int y,
                                      float z0, float k0, float3 w, int& it) {
   const int H = A.vs.H, W = A.vs.W;
   it = 0;
@@ -309,18 +327,18 @@ __device__ __forceinline__ int march(const FrameArgs& A, const DevCam& c, const 
   step_out(r, sx, sy);
   r.ka = fmaf(s0, r.dk, r.k0);
   const float thick = A.thickness;
+  // off screen is checked where the position changes: after leaving a cell, not after refining
+  if ((unsigned)r.ix >= (unsigned)W || (unsigned)r.iy >= (unsigned)H) return SSGI_HIT_MISS;
 
   for (;;) {
-    if ((unsigned)r.ix >= (unsigned)W || (unsigned)r.iy >= (unsigned)H || it >= max_steps) return SSGI_HIT_MISS;
+    if (it >= max_steps) return SSGI_HIT_MISS;
     ++it;
     exits(r, sx, sy);
     const float se = fminf(sx, sy);
     const float kb = fmaf(fminf(se, 1.0f), r.dk, r.k0);
     const float kmin = fminf(r.ka, kb), kmax = fmaxf(r.ka, kb);
     // one load for every level (level 0 is the depth buffer itself)
-    const float* base = r.L ? hz_v + s_hoff[r.L] : dep;
-    const int wl = r.L ? s_hw[r.L] : W;
-    const float hzv = __ldg(base + (r.iy >> r.L) * wl + (r.ix >> r.L));
+    const float hzv = __ldg(lt.base[r.L] + (r.iy >> r.L) * lt.w[r.L] + (r.ix >> r.L));
     const bool skip = kmin * hzv > 1.0f;
     if (!skip) {
       if (r.L > 0) {  // something in this cell may be hit: refine
@@ -335,14 +353,14 @@ __device__ __forceinline__ int march(const FrameArgs& A, const DevCam& c, const 
     step_out(r, sx, sy);
     r.ka = kb;
     if (skip && r.L + 1 < levels) ++r.L;
+    if ((unsigned)r.ix >= (unsigned)W || (unsigned)r.iy >= (unsigned)H) return SSGI_HIT_MISS;
   }
 }
 
 // Trace all samples of pixel (x, y) of `view`: GGX sampling, march, gather, Monte-Carlo sum
 // and composite (one thread per pixel).
 template <bool kCid>
-__device__ __forceinline__ float3 trace_pixel(const FrameArgs& A, int x, int y, int view,
-                                            const int* __restrict__ s_hoff, const int* __restrict__ s_hw) {
+__device__ __forceinline__ float3 trace_pixel(const FrameArgs& A, int x, int y, int view, const LevelTable& lt) {
   const int W = A.vs.W, H = A.vs.H;
   const long long HW = (long long)H * W;
   const int rem = y * W + x;
@@ -362,8 +380,6 @@ __device__ __forceinline__ float3 trace_pixel(const FrameArgs& A, int x, int y, 
   const bool brute = (A.flags & SSGI_BRUTE_FORCE) != 0;
   const int levels = brute ? 1 : A.levels;
   const int max_steps = brute ? INT_MAX : A.max_steps;
-  const float* dep = A.depth + view * HW;
-  const float* hz_v = A.hiz ? A.hiz + (long long)view * A.hz.per_view : nullptr;
 
   const float3 d = pix_dir_world(cam, x, y);
   const float3 v = d * (-1.0f / sqrtf(dot3(d, d)));
@@ -383,7 +399,7 @@ __device__ __forceinline__ float3 trace_pixel(const FrameArgs& A, int x, int y, 
     int q = SSGI_HIT_INVALID;
     if (sm.valid) {
       int it;
-      q = march(A, cam, dep, hz_v, s_hoff, s_hw, levels, max_steps, x, y, z0, k0, world_to_cam(cam, sm.w), it);
+      q = march(A, cam, lt, levels, max_steps, x, y, z0, k0, world_to_cam(cam, sm.w), it);
       steps += (unsigned long long)it;
       const float3 Li = q >= 0 ? ld3(A.c1 + 3 * (view * HW + q)) : env_lookup0(A.mips, A.e, sm.w);
       const float K = ggx_G1(sm.nw, rho) * g1v * sm.vh / (nv * sm.nh);
