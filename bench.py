@@ -57,6 +57,27 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest of every rank's x (the slowest rank sets the job's time); x itself on one rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Units all ranks processed per second when each rank does units_per_rank in ms (weak scaling)."""
+    return world * units_per_rank / (ms / 1e3)
+
+
+def rank_seed(seed: int, rank: int) -> int:
+    """Each rank renders its own frame: a different sample sequence per rank."""
+    return seed + 1000 * rank
+
+
 def workload():
     import ssgi_inputs as si
     return si.config3()
@@ -491,7 +512,7 @@ def run_ours(args):
     wl = workload()
     V, H, W = wl.depth.shape
     p = S.params_of(wl.params)
-    p.seed = p.seed + 1000 * rank  # each rank renders its own frame
+    p.seed = rank_seed(p.seed, rank)
     pipe = S.FramePipeline((V, H, W), wl.env.shape[:2], p, wl.cams)
     pipe.load(wl)
     rays = V * H * W * p.spp
@@ -524,11 +545,8 @@ def run_ours(args):
     step_ms = [ev[0].elapsed_time(ev[-1]) for ev in evs]
     stage_ms = {n: statistics.mean(ev[i].elapsed_time(ev[i + 1]) for ev in evs) for i, n in enumerate(names)}
     ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * rays / (ms / 1e3)
+    ms = max_over_ranks(ms, world)
+    value = whole_job_rate(rays, world, ms)
     trace_ms = stage_ms["trace"]
     launches = pipe.kernels_per_step() * args.steps
 
@@ -655,11 +673,8 @@ def run_ours(args):
             if k >= args.warmup:
                 e_ms.append(a.elapsed_time(b))
         em = statistics.mean(e_ms)
-        if world > 1:
-            t = torch.tensor([em], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            em = float(t.item())
-        e2e = {"value": world * rays / (em / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+        em = max_over_ranks(em, world)
+        e2e = {"value": whole_job_rate(rays, world, em), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": em}
 
     peaks, peak_src = measured_peaks()
