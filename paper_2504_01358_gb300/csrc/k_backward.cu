@@ -33,7 +33,7 @@ inline void launch_bwd_mc(const FrameArgs& A, int blocks, cudaStream_t s) {
     k_bwd_mc<false><<<blocks, 256, 0, s>>>(A);
 }
 
-__global__ void __launch_bounds__(256) k_bwd_direct(FrameArgs A) {
+__global__ void __launch_bounds__(256, 4) k_bwd_direct(FrameArgs A) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= (long long)A.vs.V * A.vs.H * A.vs.W) return;
   bwd_direct_pixel(A, p);
