@@ -43,23 +43,23 @@ __global__ void __launch_bounds__(256) k_brdf_lut(int N, int M, float* __restric
   }
 }
 
-__global__ void k_env_down(const float* __restrict__ src, int hs, int ws, float* __restrict__ dst) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (hs >> 1) * (ws >> 1) * 3) return;
-  env_down_item(src, hs, ws, dst, t);
+// Environment mips in two launches: 32 x 32 texel tiles copied and reduced through level 5 in
+// shared memory, then one block builds levels 6.. from level 5.
+__global__ void __launch_bounds__(256) k_env_tiles(const float* env0, EnvInfo e, float* mips) {
+  __shared__ TileBuf s;
+  env_tile_block(env0, e, mips, blockIdx.x, blockIdx.y, s);
 }
 
+__global__ void __launch_bounds__(256) k_env_upper(EnvInfo e, float* mips) { env_upper_block(e, mips); }
+
+// Hi-Z in two launches: 32 x 32 tiles through level 5, then one block per view for levels 6..
 __global__ void __launch_bounds__(256) k_hiz_tile(const float* __restrict__ depth, int H, int W, HizInfo hz,
                                                   float* __restrict__ hiz) {
   __shared__ TileBuf s;
   hiz_tile_block(depth, H, W, hz, hiz, blockIdx.z, blockIdx.x, blockIdx.y, s);
 }
 
-__global__ void k_hiz_level(int V, HizInfo hz, int l, float* __restrict__ hiz) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= V * hz.w[l] * hz.h[l]) return;
-  hiz_level_item(hz, l, hiz, t);
-}
+__global__ void __launch_bounds__(256) k_hiz_upper(HizInfo hz, float* hiz) { hiz_upper_block(hz, blockIdx.x, hiz); }
 
 }  // namespace ssgi
 
@@ -80,17 +80,16 @@ ssgi_status ssgi_build_env_mips(const float* env, int32_t h, int32_t w, float* m
   EnvInfo e;
   if (!env || !mips_out || make_env_dims(h, w, &e) != SSGI_OK) return SSGI_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  if (env != mips_out) {
-    if (cudaMemcpyAsync(mips_out, env, sizeof(float) * (size_t)h * w * 3, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-      return SSGI_ERR_CUDA;
+  // tiles are exact: the sizes are powers of two (env may equal mips_out: level 0 is rewritten
+  // with its own values)
+  const dim3 grid(w / (w < kHizTile ? w : kHizTile), h / (h < kHizTile ? h : kHizTile));
+  k_env_tiles<<<grid, 256, 0, s>>>(env, e, mips_out);
+  ssgi_status st = launch_status();
+  if (st == SSGI_OK && e.levels > 6) {
+    k_env_upper<<<1, 256, 0, s>>>(e, mips_out);
+    st = launch_status();
   }
-  for (int l = 1; l < e.levels; ++l) {
-    const int n = e.h[l] * e.w[l] * 3;
-    k_env_down<<<ceil_div(n, 256), 256, 0, s>>>(mips_out + e.off[l - 1], e.h[l - 1], e.w[l - 1], mips_out + e.off[l]);
-    const ssgi_status st = launch_status();
-    if (st != SSGI_OK) return st;
-  }
-  return SSGI_OK;
+  return st;
 }
 
 ssgi_status ssgi_build_hiz(const float* depth, ssgi_dims d, int32_t levels, float* hiz_out, ssgi_stream_t stream) {
@@ -103,9 +102,8 @@ ssgi_status ssgi_build_hiz(const float* depth, ssgi_dims d, int32_t levels, floa
   dim3 grid(ceil_div(d.width, kHizTile), ceil_div(d.height, kHizTile), d.views);
   k_hiz_tile<<<grid, 256, 0, s>>>(depth, d.height, d.width, hz, hiz_out);
   ssgi_status st = launch_status();
-  for (int l = 6; l < levels && st == SSGI_OK; ++l) {
-    const int n = d.views * hz.w[l] * hz.h[l];
-    k_hiz_level<<<ceil_div(n, 256), 256, 0, s>>>(d.views, hz, l, hiz_out);
+  if (st == SSGI_OK && levels > 6) {
+    k_hiz_upper<<<d.views, 256, 0, s>>>(hz, hiz_out);
     st = launch_status();
   }
   return st;

@@ -479,9 +479,11 @@ class FramePipeline:
 
     def kernels_per_step(self) -> int:
         """Kernel launches of libssgi.so in one step (as issued by the .cu entry points):
-        env mips levels-1, Hi-Z 1 + max(0, levels-6), shade 1, trace 1, loss 1, backward 3."""
-        hz = 0 if self.params.hiz_levels <= 1 else 1 + max(0, self.params.hiz_levels - 6)
-        return (self.em.levels - 1) + hz + 1 + 1 + 1 + 3
+        env mips 1 (+1 above 6 levels), Hi-Z 1 (+1 above 6 levels; none for 1 level), shade 1,
+        trace 1, loss 1, backward 3."""
+        env = 1 + (1 if self.em.levels > 6 else 0)
+        hz = 0 if self.params.hiz_levels <= 1 else 1 + (1 if self.params.hiz_levels > 6 else 0)
+        return env + hz + 1 + 1 + 1 + 3
 
     def h2d_bytes(self) -> int:
         ts = [self.g.depth, self.g.normal, self.g.albedo, self.g.rough, self.g.metal, self.env, self.target]
