@@ -479,8 +479,16 @@ __device__ __forceinline__ void dlnD(float c, float rho, float& dc, float& dr) {
 
 // Scatter g (per channel) with weight `scale` through the bilinear taps into gm, and return
 // the derivatives of the bilinear value contracted with g along x and y (texel units).
+// Plain 16-byte atomic add of v to the RGB of *p.
+__device__ __forceinline__ void atomic_add4_plain(float4* p, float3 v) {
+  atomicAdd(p, make_float4(v.x, v.y, v.z, 0.0f));
+}
+
+// aggregate: sum over the warp's lanes that share a texel first (atomic_add4).  Worth it where
+// many lanes land on one texel (the coarse levels of the direct adjoint); where they rarely do
+// (mip 0 under scattered directions) the matching costs more than it saves.
 __device__ __forceinline__ void bilin_adj(const float* __restrict__ mips, const Taps& t, float3 g, float scale,
-                                          float4* gm, float& gx, float& gy) {
+                                          float4* gm, float& gx, float& gy, bool aggregate = true) {
   const float3 a = ld3(mips + t.idx[0]), b = ld3(mips + t.idx[1]);
   const float3 c = ld3(mips + t.idx[2]), d = ld3(mips + t.idx[3]);
   gx = dot3(g, (b - a) * (1.0f - t.ty) + (d - c) * t.ty);
@@ -489,17 +497,24 @@ __device__ __forceinline__ void bilin_adj(const float* __restrict__ mips, const 
     const float w00 = (1.0f - t.tx) * (1.0f - t.ty), w01 = t.tx * (1.0f - t.ty);
     const float w10 = (1.0f - t.tx) * t.ty, w11 = t.tx * t.ty;
     // tap offsets count floats of the packed RGB chain (3 per texel); gm holds one float4 per texel
-    atomic_add4(gm + t.idx[0] / 3, g * (scale * w00));
-    atomic_add4(gm + t.idx[1] / 3, g * (scale * w01));
-    atomic_add4(gm + t.idx[2] / 3, g * (scale * w10));
-    atomic_add4(gm + t.idx[3] / 3, g * (scale * w11));
+    if (aggregate) {
+      atomic_add4(gm + t.idx[0] / 3, g * (scale * w00));
+      atomic_add4(gm + t.idx[1] / 3, g * (scale * w01));
+      atomic_add4(gm + t.idx[2] / 3, g * (scale * w10));
+      atomic_add4(gm + t.idx[3] / 3, g * (scale * w11));
+    } else {
+      atomic_add4_plain(gm + t.idx[0] / 3, g * (scale * w00));
+      atomic_add4_plain(gm + t.idx[1] / 3, g * (scale * w01));
+      atomic_add4_plain(gm + t.idx[2] / 3, g * (scale * w10));
+      atomic_add4_plain(gm + t.idx[3] / 3, g * (scale * w11));
+    }
   }
 }
 
 // Adjoint of SampleEnvMap(d, lambda): texel gradients into gm (all levels), returns d/dd and
 // d/dlambda (zero where lambda is clamped).
 __device__ __forceinline__ float3 env_lookup_adj(const float* __restrict__ mips, const EnvInfo& e, float3 d,
-                                                 float lam, float3 g, float4* gm, float& glam) {
+                                                 float lam, float3 g, float4* gm, float& glam, bool aggregate = true) {
   const float lmax = (float)(e.levels - 1);
   const bool inside = lam > 0.0f && lam < lmax;
   lam = fminf(fmaxf(lam, 0.0f), lmax);
@@ -509,8 +524,8 @@ __device__ __forceinline__ float3 env_lookup_adj(const float* __restrict__ mips,
   const DirAngles ang = dir_angles(d);
   const Taps t0 = env_taps(e, l0, ang), t1 = env_taps(e, l1, ang);
   float gx0, gy0, gx1 = 0.0f, gy1 = 0.0f;
-  bilin_adj(mips, t0, g, 1.0f - t, gm, gx0, gy0);
-  if (t != 0.0f) bilin_adj(mips, t1, g, t, gm, gx1, gy1);
+  bilin_adj(mips, t0, g, 1.0f - t, gm, gx0, gy0, aggregate);
+  if (t != 0.0f) bilin_adj(mips, t1, g, t, gm, gx1, gy1, aggregate);
   const float gu = (1.0f - t) * gx0 * (float)e.w[l0] + t * gx1 * (float)e.w[l1];
   const float gv = (1.0f - t) * gy0 * (float)e.h[l0] + t * gy1 * (float)e.h[l1];
   glam = 0.0f;
@@ -601,13 +616,15 @@ __device__ __forceinline__ void bwd_mc_pixel(const FrameArgs& A, long long p) {
       }
       float3 gdir = f3(0.f, 0.f, 0.f);  // d loss / d w through a miss's lookup
       if (q >= 0) {
-        atomic_add4(A.g_c1 + (view * HW + q), gL);
+        // receivers' hits land on scattered pixels and misses on scattered mip-0 texels: no
+        // warp aggregation in this kernel (see bilin_adj)
+        atomic_add4_plain(A.g_c1 + (view * HW + q), gL);
       } else if (kPathwise) {
         float glam;
-        gdir = env_lookup_adj(A.mips, A.e, sm.w, 0.0f, gL, A.g_mips, glam);
+        gdir = env_lookup_adj(A.mips, A.e, sm.w, 0.0f, gL, A.g_mips, glam, false);
       } else {
         float gx, gy;
-        bilin_adj(A.mips, tm, gL, 1.0f, A.g_mips, gx, gy);
+        bilin_adj(A.mips, tm, gL, 1.0f, A.g_mips, gx, gy, false);
       }
       if (kPathwise) {
         // total derivative through h(n, rho), w = 2 (v.h) h - v and the dot products
