@@ -128,91 +128,113 @@ __device__ __forceinline__ bool grid_sync(unsigned* ctl) {
   return s_ok != 0;
 }
 
+// Sizes every phase needs, computed once per block into shared memory and read back inside
+// each phase: a read after a grid barrier (which synchronises the block) cannot be merged with
+// one before it, so no value stays in a register through the trace and adjoint loops.
+struct PhaseConsts {
+  long long HW, npx, gsz;
+  int V, H, W, nchunks;
+};
+
 template <bool kCid, bool kPathwise>
 __global__ void __launch_bounds__(kFusedThreads, 8) k_step_fused(const __grid_constant__ FusedArgs F) {
   const FrameArgs& A = F.f;
+  const EnvInfo& e = A.e;
   __shared__ LevelTable s_lv;
   __shared__ TileBuf s_tile;
-  const int V = A.vs.V, H = A.vs.H, W = A.vs.W;
-  const long long HW = (long long)H * W, npx = V * HW;
-  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long gsz = (long long)gridDim.x * blockDim.x;
-  const EnvInfo& e = A.e;
-  unsigned* ctl = F.ctl;
-  stamp(ctl, 0);
+  __shared__ PhaseConsts s_k;
+  if (threadIdx.x == 0) {
+    s_k.V = A.vs.V;
+    s_k.H = A.vs.H;
+    s_k.W = A.vs.W;
+    s_k.HW = (long long)A.vs.H * A.vs.W;
+    s_k.npx = s_k.V * s_k.HW;
+    s_k.gsz = (long long)gridDim.x * kFusedThreads;
+    s_k.nchunks = (int)((s_k.npx + kFusedThreads - 1) / kFusedThreads);
+  }
+  __syncthreads();
+  stamp(F.ctl, 0);
 
   // P0: clear the backward accumulators and the loss; Hi-Z and environment pyramids, 32 x 32
   // tiles through level 5, levels 6.. by the block that finishes a pyramid's last tile.
-  for (long long i = gtid; i < F.n_gc1; i += gsz) A.g_c1[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (long long i = gtid; i < F.n_gmips; i += gsz) A.g_mips[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (gtid == 0) *F.loss = 0.0f;
   {
+    const long long gtid = (long long)blockIdx.x * kFusedThreads + threadIdx.x, gsz = s_k.gsz;
+    const int V = s_k.V, H = s_k.H, W = s_k.W;
+    for (long long i = gtid; i < F.n_gc1; i += gsz) A.g_c1[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (long long i = gtid; i < F.n_gmips; i += gsz) A.g_mips[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (gtid == 0) *F.loss = 0.0f;
     const int hx = (W + kHizTile - 1) / kHizTile, hy = (H + kHizTile - 1) / kHizTile;
     const int n_hz = A.levels > 1 ? hx * hy * V : 0;
     const int ex = e.w[0] / min(kHizTile, e.w[0]), ey = e.h[0] / min(kHizTile, e.h[0]);
-    for_each_chunk(ctl + kPyrNext, n_hz + ex * ey, [&](int t) {
+    for_each_chunk(F.ctl + kPyrNext, n_hz + ex * ey, [&](int t) {
       if (t < n_hz) {
         const int v = t / (hx * hy), r = t - v * hx * hy;
         hiz_tile_block(A.depth, H, W, A.hz, F.hiz, v, r % hx, r / hx, s_tile);
-        if (A.levels > 6 && last_arrival(ctl + kHizDone + v, hx * hy)) hiz_upper_block(A.hz, v, F.hiz);
+        if (A.levels > 6 && last_arrival(F.ctl + kHizDone + v, hx * hy)) hiz_upper_block(A.hz, v, F.hiz);
       } else {
         const int r = t - n_hz;
         env_tile_block(F.env, e, F.mips, r % ex, r / ex, s_tile);
-        if (e.levels > 6 && last_arrival(ctl + kEnvDone, ex * ey)) env_upper_block(e, F.mips);
+        if (e.levels > 6 && last_arrival(F.ctl + kEnvDone, ex * ey)) env_upper_block(e, F.mips);
       }
     });
   }
-  if (!grid_sync(ctl)) return;
-  stamp(ctl, 1);
+  if (!grid_sync(F.ctl)) return;
+  stamp(F.ctl, 1);
 
   // P1: direct shading
-  for (long long p = gtid; p < npx; p += gsz) shade_pixel(A, p);
-  if (!grid_sync(ctl)) return;
-  stamp(ctl, 2);
+  {
+    const long long npx = s_k.npx, gsz = s_k.gsz;
+    for (long long p = (long long)blockIdx.x * kFusedThreads + threadIdx.x; p < npx; p += gsz) shade_pixel(A, p);
+  }
+  if (!grid_sync(F.ctl)) return;
+  stamp(F.ctl, 2);
 
   // P2: trace, one 8 x 16 tile per block iteration, and the L2 loss of each finished pixel.
   // The per-tile cost varies by an order of magnitude (sky vs. rays that run out of steps),
   // so blocks take the next tile from a counter instead of a fixed stride.
   {
-    const float inv = 1.0f / (float)(npx * 3);
     float acc = 0.0f;
-    const int tx = (W + 7) / 8, ty = (H + 15) / 16;
-    for_each_chunk(ctl + kTraceNext, tx * ty * V, [&](int t) {
+    const int tx = (s_k.W + 7) / 8, ty = (s_k.H + 15) / 16;
+    for_each_chunk(F.ctl + kTraceNext, tx * ty * s_k.V, [&](int t) {
       const int v = t / (tx * ty), r = t - v * tx * ty;
       const int x = (r % tx) * 8 + (threadIdx.x % 8), y = (r / tx) * 16 + (threadIdx.x / 8);
       fill_levels(A, v, s_lv);  // the previous tile's reads ended at for_each_chunk's barriers
       __syncthreads();
-      if (x < W && y < H) {
+      if (x < s_k.W && y < s_k.H) {
         const float3 fin = trace_pixel<kCid>(A, x, y, v, s_lv);
-        const long long p = v * HW + (long long)y * W + x;
+        const long long p = v * s_k.HW + (long long)y * s_k.W + x;
+        const float inv = 1.0f / (float)(s_k.npx * 3);
         acc += (A.flags & SSGI_SRGB_LOSS) ? l2_srgb_pixel(A, p, fin, inv) : l2_pixel(A, p, fin, inv);
       }
     });
-    block_sum_add(acc, F.loss, inv);
+    block_sum_add(acc, F.loss, 1.0f / (float)(s_k.npx * 3));
   }
-  if (!grid_sync(ctl)) return;
-  stamp(ctl, 3);
+  if (!grid_sync(F.ctl)) return;
+  stamp(F.ctl, 3);
 
   // P3: Monte-Carlo adjoint (scatters into g_c1 and g_mips)
-  const int nchunks = (int)((npx + kFusedThreads - 1) / kFusedThreads);
-  for_each_chunk(ctl + kMcNext, nchunks, [&](int c) {
+  for_each_chunk(F.ctl + kMcNext, s_k.nchunks, [&](int c) {
     const long long p = (long long)c * kFusedThreads + threadIdx.x;
-    if (p < npx) bwd_mc_pixel<kPathwise>(A, p);
+    if (p < s_k.npx) bwd_mc_pixel<kPathwise>(A, p);
   });
-  if (!grid_sync(ctl)) return;
-  stamp(ctl, 4);
+  if (!grid_sync(F.ctl)) return;
+  stamp(F.ctl, 4);
 
   // P4: direct-shading adjoint
-  for_each_chunk(ctl + kDirNext, nchunks, [&](int c) {
+  for_each_chunk(F.ctl + kDirNext, s_k.nchunks, [&](int c) {
     const long long p = (long long)c * kFusedThreads + threadIdx.x;
-    if (p < npx) bwd_direct_pixel(A, p);
+    if (p < s_k.npx) bwd_direct_pixel(A, p);
   });
-  if (!grid_sync(ctl)) return;
-  stamp(ctl, 5);
+  if (!grid_sync(F.ctl)) return;
+  stamp(F.ctl, 5);
 
   // P5: mip-chain adjoint to the base texels
-  for (long long t = gtid; t < (long long)e.h[0] * e.w[0] * 3; t += gsz) bwd_env_item(e, A.g_mips, F.g_env, (int)t);
-  stamp(ctl, 6);
+  {
+    const long long gsz = s_k.gsz, n = (long long)e.h[0] * e.w[0] * 3;
+    for (long long t = (long long)blockIdx.x * kFusedThreads + threadIdx.x; t < n; t += gsz)
+      bwd_env_item(e, A.g_mips, F.g_env, (int)t);
+  }
+  stamp(F.ctl, 6);
 }
 
 struct FusedLayout {
