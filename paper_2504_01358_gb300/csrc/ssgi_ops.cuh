@@ -330,15 +330,25 @@ __device__ __forceinline__ int march(const FrameArgs& A, const DevCam& c, const 
   // off screen is checked where the position changes: after leaving a cell, not after refining
   if ((unsigned)r.ix >= (unsigned)W || (unsigned)r.iy >= (unsigned)H) return SSGI_HIT_MISS;
 
+  // The loop is exits() and step_out() written out on the cell's corner and exit edges, which
+  // gives the same integers and floats with fewer integer operations (the march is bound by
+  // the ALU pipe): with cs = 2^L and ix >= 0, (ix >> L) << L = ix & -cs, the exit edge
+  // ((ix >> L) + sgx) << L = lo_x + sgx cs, the pixel across it is that edge + sgx - 1, and
+  // the cell's pyramid index (iy >> L) w + (ix >> L) = (lo_y w + lo_x) >> L exactly (a sum of
+  // multiples of cs; lo_y w < 2^28 by the size limits).
   for (;;) {
     if (it >= max_steps) return SSGI_HIT_MISS;
     ++it;
-    exits(r, sx, sy);
+    const int cs = 1 << r.L;
+    const int lo_x = r.ix & -cs, lo_y = r.iy & -cs;
+    const int bx = lo_x + r.sgx * cs, by = lo_y + r.sgy * cs;
+    const float sx = fmaf((float)bx, r.iDx, r.ox);
+    const float sy = fmaf((float)by, r.iDy, r.oy);
     const float se = fminf(sx, sy);
     const float kb = fmaf(fminf(se, 1.0f), r.dk, r.k0);
     const float kmin = fminf(r.ka, kb), kmax = fmaxf(r.ka, kb);
     // one load for every level (level 0 is the depth buffer itself)
-    const float hzv = __ldg(lt.base[r.L] + (r.iy >> r.L) * lt.w[r.L] + (r.ix >> r.L));
+    const float hzv = __ldg(lt.base[r.L] + ((lo_y * lt.w[r.L] + lo_x) >> r.L));
     const bool skip = kmin * hzv > 1.0f;
     if (!skip) {
       if (r.L > 0) {  // something in this cell may be hit: refine
@@ -350,9 +360,15 @@ __device__ __forceinline__ int march(const FrameArgs& A, const DevCam& c, const 
     // leave the cell: skipped at any level, or passed behind a level-0 pixel (one code path for
     // both, so a warp whose lanes do either runs it once)
     if (!(se < 1.0f)) return SSGI_HIT_MISS;  // the cell holds the end of the segment
-    step_out(r, sx, sy);
+    const bool xe = sx <= sy;
+    const int f = __float2int_rd(xe ? fmaf(sx, r.Dy, r.P0y) : fmaf(sy, r.Dx, r.P0x));
+    const int lo_o = xe ? lo_y : lo_x;
+    const int along = min(max(f, lo_o), lo_o + cs - 1);
+    const int across = xe ? bx + r.sgx - 1 : by + r.sgy - 1;
+    r.ix = xe ? across : along;
+    r.iy = xe ? along : across;
     r.ka = kb;
-    if (skip && r.L + 1 < levels) ++r.L;
+    r.L = min(r.L + (int)skip, levels - 1);  // up a level after a skip, up to the top
     if ((unsigned)r.ix >= (unsigned)W || (unsigned)r.iy >= (unsigned)H) return SSGI_HIT_MISS;
   }
 }
