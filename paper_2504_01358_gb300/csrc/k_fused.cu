@@ -136,8 +136,10 @@ struct PhaseConsts {
   int V, H, W, nchunks;
 };
 
+// Seven resident blocks per SM (72 registers a thread): fewer spills in the trace phase than at
+// eight blocks and 64 registers, which measured slower (as did six at 80).
 template <bool kCid, bool kPathwise>
-__global__ void __launch_bounds__(kFusedThreads, 8) k_step_fused(const __grid_constant__ FusedArgs F) {
+__global__ void __launch_bounds__(kFusedThreads, 7) k_step_fused(const __grid_constant__ FusedArgs F) {
   const FrameArgs& A = F.f;
   const EnvInfo& e = A.e;
   __shared__ LevelTable s_lv;

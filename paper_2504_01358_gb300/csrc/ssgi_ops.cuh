@@ -237,9 +237,12 @@ __device__ __forceinline__ void shade_pixel(const FrameArgs& A, long long p) {
 // Per-level base pointer and row width of the pyramid of one view, level 0 being the depth
 // buffer itself, so that the march reads every level through the same code (shared memory,
 // filled by the block for the view it traces).
+struct __align__(16) LevelEntry {  // one 16-byte shared-memory load per march iteration
+  const float* base;
+  int w, pad;
+};
 struct LevelTable {
-  const float* base[SSGI_MAX_HIZ_LEVELS];
-  int w[SSGI_MAX_HIZ_LEVELS];
+  LevelEntry lv[SSGI_MAX_HIZ_LEVELS];
 };
 
 // Block-level part: threads 0..SSGI_MAX_HIZ_LEVELS-1 fill the table; the caller synchronises.
@@ -247,9 +250,10 @@ __device__ __forceinline__ void fill_levels(const FrameArgs& A, int view, LevelT
   const int l = threadIdx.x;
   if (l < SSGI_MAX_HIZ_LEVELS) {
     const long long HW = (long long)A.vs.H * A.vs.W;
-    t.base[l] = l == 0 ? A.depth + view * HW
-                       : (A.hiz && l < A.hz.levels ? A.hiz + (long long)view * A.hz.per_view + A.hz.off[l] : nullptr);
-    t.w[l] = l == 0 ? A.vs.W : A.hz.w[l];
+    t.lv[l].base = l == 0 ? A.depth + view * HW
+                          : (A.hiz && l < A.hz.levels ? A.hiz + (long long)view * A.hz.per_view + A.hz.off[l] : nullptr);
+    t.lv[l].w = l == 0 ? A.vs.W : A.hz.w[l];
+    t.lv[l].pad = 0;
   }
 }
 
@@ -348,7 +352,8 @@ __device__ __forceinline__ int march(const FrameArgs& A, const DevCam& c, const 
     const float kb = fmaf(fminf(se, 1.0f), r.dk, r.k0);
     const float kmin = fminf(r.ka, kb), kmax = fmaxf(r.ka, kb);
     // one load for every level (level 0 is the depth buffer itself)
-    const float hzv = __ldg(lt.base[r.L] + ((lo_y * lt.w[r.L] + lo_x) >> r.L));
+    const LevelEntry le = lt.lv[r.L];
+    const float hzv = __ldg(le.base + ((lo_y * le.w + lo_x) >> r.L));
     const bool skip = kmin * hzv > 1.0f;
     if (!skip) {
       if (r.L > 0) {  // something in this cell may be hit: refine
