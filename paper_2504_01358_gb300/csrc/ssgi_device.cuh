@@ -100,9 +100,13 @@ __device__ __forceinline__ float f0_of(float a, float m) { return 0.04f * (1.0f 
 // cos^2 = (1 - xi0) / den and sin^2 = rho^2 xi0 / den with den = 1 + (rho^2 - 1) xi0: the
 // same values as sqrt(1 - cos^2) without its cancellation for near-mirror lobes.  *ct
 // receives cos(theta_h) = n.h.
+// den = 1 + (rho^2 - 1) xi0 is formed as (1 - xi0) + rho^2 xi0: the same number without the
+// cancellation of the first form as xi0 -> 1 (1 - xi0 is exact on the uniforms' 2^-24 grid), so
+// that cos^2 + sin^2 stays 1 to a few ulp and h stays a unit vector; with the first form a
+// low-roughness sample's h could be ~1e-5 too long, turning its reflection by as much.
 __device__ __forceinline__ float3 ggx_sample_h(float3 n, float rho, float xi0, float xi1, float* ct_out = nullptr) {
   const float a2 = rho * rho;
-  const float den = fmaf(a2 - 1.0f, xi0, 1.0f);
+  const float den = fmaf(a2, xi0, 1.0f - xi0);
   const float ct = sqrtf((1.0f - xi0) / den);
   const float st = sqrtf(a2 * xi0 / den);
   if (ct_out) *ct_out = ct;
@@ -122,7 +126,7 @@ __device__ __forceinline__ float3 ggx_sample_h(float3 n, float rho, float xi0, f
 // d cos / d rho = -cos rho xi0 / den; the frame's derivatives follow from aa' = aa^2 (n.z).
 __device__ __forceinline__ void ggx_sample_h_jac(float3 n, float rho, float xi0, float xi1, float3 dh[4]) {
   const float a2 = rho * rho;
-  const float den = fmaf(a2 - 1.0f, xi0, 1.0f);
+  const float den = fmaf(a2, xi0, 1.0f - xi0);
   const float ct = sqrtf((1.0f - xi0) / den);
   const float q = sqrtf(xi0 / den);
   const float st = rho * q;
