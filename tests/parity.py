@@ -6,8 +6,18 @@ Tolerances (written here, used by every parity test):
     near-tie in the oracle (decision margin < MARGIN_TOL), i.e. a rounding-order case;
   * per-pixel RGB: |gpu - oracle|_inf <= RGB_RTOL * max(|oracle|_inf, RGB_FLOOR) on pixels
     whose samples all match;
+  * a pixel above that bound must be explained by its own conditioning (checked when the test
+    passes the workload): the FP32 direction of a missed sample differs from the oracle's by a few
+    roundings (DIR_EPS per component), and where the latitude-longitude lookup is steep in the
+    direction (near the map's poles, where the longitude atan2(x, -z) is ill-conditioned, or
+    across a bright texel) that changes the sample's radiance by far more than a rounding; such a
+    pixel may exceed RGB_RTOL_MAX by at most the sum over its missed samples of |weight| x the
+    largest change of the lookup under a DIR_EPS move of the direction, and such pixels are at
+    most OUTLIER_SHARE_MAX of the compared ones;
   * gradients: <= GRAD_RTOL relative (per element against the vector's scale, and as a norm).
 """
+import math
+
 import numpy as np
 
 import oracle as O
@@ -19,6 +29,10 @@ RGB_FRAC_MIN = 0.99999  # share of pixels within RGB_RTOL (all pixels below 1e5 
 RGB_RTOL_MAX = 3e-4     # bound for the rest: FP32 direction error (~1e-7 rad) x env texel contrast
 RGB_FLOOR = 1e-3
 GRAD_RTOL = 1e-3
+DIR_EPS = 1e-6          # FP32 error of a sampled direction's components: ~8 ulp of 1 (normalisation,
+                        # the GGX sample's square roots and sine/cosine, the reflection)
+OUTLIER_SHARE_MAX = 1e-3
+ANGLE_EPS = 4.0 / 2 ** 24  # FP32 rounding of a lookup's longitude and latitude, in turns
 
 
 def assert_rgb(err, label):
@@ -77,18 +91,155 @@ def compare_hits(h_gpu, r_orc):
     return frac, bad, margins
 
 
-def assert_forward_parity(gpu, orc, label=""):
+def direction_bound(wl, view, y, x, hits, flags, eps=DIR_EPS):
+    """Per-channel bound on |gpu - oracle| of pixel (x, y)'s Monte-Carlo sums from the
+    conditioning of its missed samples' environment lookups (Sec. 3.3 estimator; the lookup is
+    the oracle's): each valid missed sample adds |weight| x the largest change of its lookup when
+    one component of the direction moves by +-eps.  Hits gather c1 at an index both sides agree
+    on and add nothing.  The samples are redrawn with the oracle's own generator and GGX sampler."""
+    V, H, W = wl.depth.shape
+    He, We = wl.env.shape[:2]
+    mips = _mips_of(wl)
+    cam = wl.cams[view].astype(np.float64)
+    R = cam[:12].reshape(3, 4)[:, :3]
+    f = (H / 2.0) / math.tan(cam[12] / 2.0)
+    d = R @ np.array([(x + 0.5 - W / 2.0) / f, -(y + 0.5 - H / 2.0) / f, -1.0])
+    v = -d / np.linalg.norm(d)
+    n = wl.normal[view, y, x].astype(np.float64)
+    rho, m = float(wl.rough[view, y, x]), float(wl.metal[view, y, x])
+    a = wl.albedo[view, y, x].astype(np.float64)
+    nv = float(n @ v)
+    F0 = 0.04 * (1.0 - m) + a * m
+    seed, spp = wl.params.seed, wl.params.spp
+    key = np.array([seed & 0xffffffff, (seed >> 32) ^ view], np.uint32)
+    out = np.zeros(3)
+    for s in range(spp):
+        if hits[s] != -1:
+            continue  # a hit, an invalid sample or background
+        o = O.philox4x32_10(np.array([y * W + x, s, 0, 0], np.uint32), key)
+        xi0, xi1 = float(int(o[0]) >> 8) / 16777216.0, float(int(o[1]) >> 8) / 16777216.0
+        h = O.ggx_sample_h(n, rho, xi0, xi1)
+        vh, nh = float(v @ h), float(n @ h)
+        w = 2.0 * vh * h - v
+        nw = float(n @ w)
+        if not (nv > 0 and nw > 0 and vh > 0 and nh > 0):
+            continue
+        Li = O.env_lookup(mips, He, We, w, 0.0)
+        dev = np.zeros(3)
+        for k in range(3):
+            for sg in (1.0, -1.0):
+                w2 = w.copy()
+                w2[k] += sg * eps
+                dev = np.maximum(dev, np.abs(O.env_lookup(mips, He, We, w2 / np.linalg.norm(w2), 0.0) - Li))
+        K = O.ggx_G1(nw, rho) * O.ggx_G1(nv, rho) * vh / (nv * nh)
+        out += (F0 + (1.0 - F0) * (1.0 - vh) ** 5) * K * dev / spp
+        if flags & O.FLAG_DIFFUSE_INDIRECT:
+            pdf = O.ggx_D(nh, rho) * nh / (4.0 * vh)
+            if pdf > 0 and np.isfinite(pdf):
+                out += (1.0 - m) * a / math.pi * nw / pdf * dev / spp
+    return out
+
+
+_MIPS = {}
+
+
+def _mips_of(wl):
+    k = id(wl.env)
+    if k not in _MIPS:
+        _MIPS.clear()
+        _MIPS[k] = O.build_env_mips(wl.env)
+    return _MIPS[k]
+
+
+def assert_forward_parity(gpu, orc, label="", wl=None, pix=None, flags=0):
+    """Hits and images of a forward pass against the oracle (module docstring).  With the
+    workload `wl` (and `pix`, the linear pixel indices of a sampled comparison), a pixel over the
+    RGB bounds passes if its conditioning explains it (direction_bound)."""
     frac, bad, margins = compare_hits(gpu["hit_idx"], orc)
     assert frac >= HIT_MATCH_MIN, f"{label}: hit-index match {frac:.6f}"
     assert np.all(margins < MARGIN_TOL), f"{label}: mismatch with decision margin {margins.max()}"
     pix_ok = ~bad.any(axis=-1)
     scale = np.maximum(np.abs(orc["final"]).max(axis=-1), RGB_FLOOR)
+    bounds = {}
     for key in [k for k in ("final", "cs_mc", "c_id") if k in gpu]:
         okey = {"c_id": "cid"}.get(key, key)
         # error of each channel in units of the pixel's output RGB
-        err = (np.abs(gpu[key].astype(np.float64) - orc[okey]).max(axis=-1) / scale)[pix_ok]
-        assert_rgb(err, f"{label}: {key}")
+        err_all = np.abs(gpu[key].astype(np.float64) - orc[okey]).max(axis=-1) / scale
+        err = err_all[pix_ok]
+        if wl is None:
+            assert_rgb(err, f"{label}: {key}")
+            continue
+        out = np.argwhere(pix_ok & (err_all > RGB_RTOL))
+        assert len(out) <= OUTLIER_SHARE_MAX * max(int(pix_ok.sum()), 1), \
+            f"{label}: {key}: {len(out)} of {int(pix_ok.sum())} pixels above {RGB_RTOL}"
+        V, H, W = wl.depth.shape
+        for idx in out:
+            t = tuple(int(i) for i in idx)
+            lin = int(pix[t[0]]) if pix is not None else (t[0] * H + t[1]) * W + t[2]
+            if lin not in bounds:
+                vv, rem = divmod(lin, H * W)
+                bounds[lin] = direction_bound(wl, vv, rem // W, rem % W, gpu["hit_idx"][t], flags).max()
+            allowed = RGB_RTOL_MAX + bounds[lin] / scale[t]
+            assert err_all[t] <= allowed, \
+                f"{label}: {key}: pixel {lin} rel err {err_all[t]:.3e} > {allowed:.3e} (conditioning bound)"
     return frac, int(bad.sum())
+
+
+def forward_outliers(gpu, orc):
+    """Pixels whose samples all hit alike but whose RGB differs by more than RGB_RTOL: the ones
+    assert_forward_parity admits only through their conditioning (direction_bound).  Their own
+    material gradients are linear in the same radiance, so they inherit its conditioning."""
+    same = ~(gpu["hit_idx"] != orc["hit_idx"]).any(axis=-1)
+    scale = np.maximum(np.abs(orc["final"]).max(axis=-1), RGB_FLOOR)
+    out = np.zeros(same.shape, bool)
+    for key in [k for k in ("final", "cs_mc", "c_id") if k in gpu]:
+        okey = {"c_id": "cid"}.get(key, key)
+        out |= np.abs(gpu[key].astype(np.float64) - orc[okey]).max(axis=-1) / scale > RGB_RTOL
+    return out & same
+
+
+def direct_kinks(wl, eps=DIR_EPS):
+    """Foreground pixels whose direct-shading lookups (Sec. 3.2) lie within the FP32 rounding of
+    a kink of their bilinear filters, where the adjoint is one-sided and the two sides may take
+    different branches: the latitude-longitude lookups at r = 2 (v.n) n - v and at n, on levels
+    floor(lambda) and floor(lambda) + 1, within eps x (texels per unit of direction) of a
+    texel-centre line; lambda = log2(rho + 1) lambda_max within eps lambda_max of an integer;
+    n.v within eps N of a texel centre of the N x N BRDF table."""
+    V, H, W = wl.depth.shape
+    He, We = wl.env.shape[:2]
+    lmax = O.env_levels(He, We) - 1
+    xs, ys = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
+    kink = np.zeros((V, H, W), bool)
+    for view in range(V):
+        cam = wl.cams[view].astype(np.float64)
+        R = cam[:12].reshape(3, 4)[:, :3]
+        f = (H / 2.0) / math.tan(cam[12] / 2.0)
+        d = np.stack([(xs - W / 2.0) / f, -(ys - H / 2.0) / f, -np.ones_like(xs)], -1) @ R.T
+        v = -d / np.linalg.norm(d, axis=-1, keepdims=True)
+        n = wl.normal[view].astype(np.float64)
+        nv = np.sum(n * v, -1)
+        lam = np.log2(wl.rough[view].astype(np.float64) + 1.0) * lmax
+        l0 = np.clip(np.floor(lam), 0, lmax).astype(np.int64)
+        levels = (l0, np.minimum(l0 + 1, lmax))
+        k = np.abs(lam - np.round(lam)) < eps * lmax
+        # r is computed (an error of eps per component, i.e. eps / q in longitude and eps in
+        # latitude); n is an input, exact on both sides, and only its angles are rounded
+        # (ANGLE_EPS of a turn; at the exact pole both sides take the same longitude)
+        for dv, de, da in ((2.0 * nv[..., None] * n - v, eps, 0.0), (n, 0.0, ANGLE_EPS)):
+            q = np.hypot(dv[..., 0], dv[..., 2])
+            u = 0.5 + np.arctan2(dv[..., 0], -dv[..., 2]) / (2.0 * math.pi)
+            vt = np.arctan2(q, dv[..., 1]) / math.pi
+            du = np.where(q > 0, de / (2.0 * math.pi * np.maximum(q, 1e-30)) + da, 0.0)
+            dvt = de / math.pi + da
+            for lv in levels:
+                wl_, hl = (We >> lv).astype(np.float64), (He >> lv).astype(np.float64)
+                tx, ty = u * wl_ - 0.5, vt * hl - 0.5
+                k |= np.abs(tx - np.round(tx)) < du * wl_
+                k |= np.abs(ty - np.round(ty)) < dvt * hl
+        tm = np.clip(nv, 0.0, 1.0) * O.LUT_N - 0.5
+        k |= np.abs(tm - np.round(tm)) < eps * O.LUT_N
+        kink[view] = k
+    return kink & np.isfinite(wl.depth) & (wl.depth > 0)
 
 
 def affected_pixels(h_gpu, h_orc):

@@ -1,6 +1,7 @@
 """GPU (libssgi.so through the C ABI) vs the FP64 oracle, element by element on the same seeded
 inputs.  Sizes span several tiles with ragged tails; config 2 runs at full size (1600x900,
-16 spp) in the bench's launch configuration and is checked on a pixel sample."""
+16 spp) in the bench's launch configuration and is checked on a pixel sample, and the bench's
+whole step (config 3: forward, loss gradient, backward) is checked at full size on every pixel."""
 import dataclasses
 
 import numpy as np
@@ -9,8 +10,8 @@ import torch
 
 import oracle as O
 import ssgi_inputs as si
-from parity import (GRAD_RTOL, affected_pixels, assert_forward_parity, assert_rgb, gpu_forward, orc_forward,
-                    pixel_rel_err)
+from parity import (GRAD_RTOL, affected_pixels, assert_forward_parity, assert_rgb, direct_kinks,
+                    forward_outliers, gpu_forward, orc_forward, pixel_rel_err)
 
 pytestmark = pytest.mark.gpu
 
@@ -109,7 +110,7 @@ def test_config2_full_size_sampled(S, olut):
     pl = np.sort(rng.choice(V * H * W, size=30000, replace=False))
     r = O.forward(wl, lut=olut, pix_list=pl)
     sub = {k: g[k].reshape((V * H * W,) + g[k].shape[3:])[pl] for k in ("hit_idx", "final", "cs_mc", "c_id")}
-    assert_forward_parity(sub, r, "config2 sample")
+    assert_forward_parity(sub, r, "config2 sample", wl=wl, pix=pl)
     # the Hi-Z pyramid and direct pass at full size
     assert np.array_equal(g["hiz"][: r["hiz"].size], r["hiz"].astype(np.float32).reshape(-1))
     assert_rgb(pixel_rel_err(g["c1"], r["c1"]).ravel(), "config2 c1")
@@ -177,7 +178,7 @@ def test_invalid_arguments_are_rejected(S):
 # --------------------------------------------------------------------------------------------
 # backward
 # --------------------------------------------------------------------------------------------
-def _backward_pair(S, wl, olut, flags):
+def _backward_pair(S, wl, olut, flags, forward_out=None):
     g = gpu_forward(wl, flags=flags)
     r = orc_forward(wl, lut=olut, flags=flags)
     target = wl.target.astype(np.float64)
@@ -190,6 +191,8 @@ def _backward_pair(S, wl, olut, flags):
     gorc = O.backward(wl.depth, wl.normal, wl.albedo, wl.rough, wl.metal, wl.cams, r["mips"], He, We, olut, r["c1"],
                       r["hit_idx"], g_final, wl.params.spp, wl.params.seed, flags)
     aff = affected_pixels(g["hit_idx"], r["hit_idx"])
+    if forward_out is not None:
+        forward_out.update(gpu=g, orc=r)
     return ggpu, gorc, aff
 
 
@@ -199,16 +202,54 @@ def test_backward_matches_oracle_adjoint(S, olut, request, name, flags):
     wl = request.getfixturevalue(name)
     if wl.target is None:
         wl = dataclasses.replace(wl, target=si.uniform_target(99, *wl.depth.shape))
-    ggpu, gorc, aff = _backward_pair(S, wl, olut, flags)
+    _assert_backward_parity(*_backward_pair(S, wl, olut, flags))
+
+
+def _assert_backward_parity(ggpu, gorc, aff, excuse=None, excused_max=0):
+    """Per-pixel gradients within GRAD_RTOL of their scale outside `aff`; with `excuse`, a pixel
+    over the bound must be one of the excused pixels (at most `excused_max` of them)."""
     ok = ~aff
     for k in ("albedo", "rough", "metal", "normal"):
-        a, b = ggpu[k][ok], gorc[k][ok]
-        scale = np.abs(b).max()
-        err = np.abs(a - b).max() / scale
-        assert err <= GRAD_RTOL, (k, err)
+        scale = np.abs(gorc[k][ok]).max()
+        err = np.abs(ggpu[k] - gorc[k]) / scale
+        if err.ndim == ok.ndim + 1:
+            err = err.max(axis=-1)
+        over = ok & (err > GRAD_RTOL)
+        if excuse is not None:
+            assert not (over & ~excuse).any(), (k, float(err[over & ~excuse].max()))
+            assert int(over.sum()) <= excused_max, (k, int(over.sum()))
+        else:
+            assert not over.any(), (k, float(err[ok].max()))
     a, b = ggpu["env"], gorc["env"]
     rel = np.linalg.norm(a - b) / np.linalg.norm(b)
     assert rel <= GRAD_RTOL, ("env", rel)
+
+
+@pytest.mark.parametrize("flags", [0, 1])
+def test_config3_full_size_backward(S, olut, flags):
+    """The benchmark's step at full size (1600x900, 16 spp, 64 steps, 8 levels: forward, L2 loss
+    gradient, ssgi_backward with its workspace, as bench.py launches them) against the oracle's
+    forward and adjoint on every pixel and every texel of the map; pixels whose samples hit
+    differently on the two sides, and the pixels those samples reach, are left out (a small
+    share, asserted)."""
+    wl = si.config3()
+    assert wl.target is not None
+    fw = {}
+    ggpu, gorc, aff = _backward_pair(S, wl, olut, flags, forward_out=fw)
+    # the forward at full size on every pixel: hits, images (the same bounds as every forward test)
+    assert_forward_parity(fw["gpu"], fw["orc"], f"config3 flags={flags}", wl=wl, flags=flags)
+    # a mismatching sample leaves out at most three pixels (its receiver and the two pixels hit),
+    # so the forward bound (>= 99.9 % of samples equal) allows up to 3 x 16 x 0.1 % of the
+    # pixels; about 0.1 % are left out at this size
+    assert aff.mean() < 0.01, float(aff.mean())
+    # A pixel's gradient may exceed the bound only where it is not defined to FP32 precision:
+    # where its forward error is admitted through the conditioning of its own environment
+    # lookups (a sample near the map's pole with a large weight: its albedo, normal and roughness
+    # gradients are linear in that radiance), or where a direct-shading lookup sits within
+    # rounding of a kink of its bilinear filter (the adjoint is one-sided there and the two sides
+    # may take different branches).  Such pixels over the bound must be few.
+    excuse = forward_outliers(fw["gpu"], fw["orc"]) | direct_kinks(wl)
+    _assert_backward_parity(ggpu, gorc, aff, excuse=excuse, excused_max=int(1e-5 * aff.size) + 1)
 
 
 @pytest.mark.parametrize("flags", [0, 1])
