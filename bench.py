@@ -180,6 +180,9 @@ def profile_summary(path=TRACE_PROFILE, files=TRACE_SOURCES):
                 if ":" in line and not line.startswith((" ", "#")):
                     k, v = line.split(":", 1)
                     kv[k.strip()] = v.strip()
+                elif line.startswith("    ") and len(line.split()) == 2:  # "    metric   value"
+                    k, v = line.split()
+                    kv.setdefault(k, v)
         return kv if kv.get("kernel_source_sha256_16") == kernel_source_hash(files) else None
     except OSError:
         return None
@@ -749,6 +752,9 @@ def run_ours(args):
                 "l2_achieved_gbs": None if l2_bytes is None else l2_bytes / (trace_ms / 1e3) / 1e9,
                 "l2_peak_gbs": bw["l2_read_gbs"],
                 "warp_execution_efficiency": profiled(prof, "warp_execution_efficiency"),
+                # the pipe that bounds the march (integer/logic ALU) and issue, as ncu measured them
+                "alu_pipe_busy_pct": profiled(prof, "alu_pipe_pct"),
+                "issue_active_pct": profiled(prof, "issue_active_pct"),
                 "profile": None if prof is None else os.path.relpath(TRACE_PROFILE, ROOT)}
 
     fused = None
