@@ -3,11 +3,18 @@ and through the FP64 oracle on the same seeded inputs, and compare.
 
 Tolerances (written here, used by every parity test):
   * hit indices: bit-exact on >= 99.9 % of samples; every mismatching sample must be a
-    near-tie in the oracle (decision margin < MARGIN_TOL), i.e. a rounding-order case;
+    near-tie in the oracle (decision margin < MARGIN_TOL), i.e. a rounding-order case.  The
+    largest margin a rounding case can have is a positional one (the distance in pixels of an
+    exit point to a pixel boundary) at the far end of a long ray: the FP32 direction error
+    (DIR_EPS) displaces a point l pixels down the ray by about l x DIR_EPS x z0 / z pixels, so
+    with l up to the screen diagonal (1836 px at 1600x900) and z0 / z up to 2 it reaches
+    ~3.7e-3 px (measured: 2.06e-3 at the end of a 440-pixel ray, the largest of 5482 mismatches
+    among the 263 M samples of the 8-view 1245x825 workload);
   * per-pixel RGB: |gpu - oracle|_inf <= RGB_RTOL * max(|oracle|_inf, RGB_FLOOR) on pixels
     whose samples all match;
   * a pixel above that bound must be explained by its own conditioning (checked when the test
-    passes the workload): the FP32 direction of a missed sample differs from the oracle's by a few
+    passes the workload; a hit sample carries the two sides' difference of the c1 it gathers,
+    itself checked by the direct-shading tests): the FP32 direction of a missed sample differs from the oracle's by a few
     roundings (DIR_EPS per component), and where the latitude-longitude lookup is steep in the
     direction (near the map's poles, where the longitude atan2(x, -z) is ill-conditioned, or
     across a bright texel) that changes the sample's radiance by far more than a rounding; such a
@@ -23,7 +30,7 @@ import numpy as np
 import oracle as O
 
 HIT_MATCH_MIN = 0.999
-MARGIN_TOL = 2e-3
+MARGIN_TOL = 5e-3
 RGB_RTOL = 1e-4
 RGB_FRAC_MIN = 0.99999  # share of pixels within RGB_RTOL (all pixels below 1e5 pixels)
 RGB_RTOL_MAX = 3e-4     # bound for the rest: FP32 direction error (~1e-7 rad) x env texel contrast
@@ -91,12 +98,14 @@ def compare_hits(h_gpu, r_orc):
     return frac, bad, margins
 
 
-def direction_bound(wl, view, y, x, hits, flags, eps=DIR_EPS):
+def direction_bound(wl, view, y, x, hits, flags, eps=DIR_EPS, c1_diff=None):
     """Per-channel bound on |gpu - oracle| of pixel (x, y)'s Monte-Carlo sums from the
-    conditioning of its missed samples' environment lookups (Sec. 3.3 estimator; the lookup is
+    conditioning of its missed samples' environment lookups (a background pixel: of its own
+    lookup in the view direction) (Sec. 3.3 estimator; the lookup is
     the oracle's): each valid missed sample adds |weight| x the largest change of its lookup when
-    one component of the direction moves by +-eps.  Hits gather c1 at an index both sides agree
-    on and add nothing.  The samples are redrawn with the oracle's own generator and GGX sampler."""
+    one component of the direction moves by +-eps.  A hit gathers c1 at an index both sides agree
+    on, and adds |weight| x the two sides' difference of that c1 (`c1_diff`, [V,H,W,3], when
+    given).  The samples are redrawn with the oracle's own generator and GGX sampler."""
     V, H, W = wl.depth.shape
     He, We = wl.env.shape[:2]
     mips = _mips_of(wl)
@@ -111,11 +120,14 @@ def direction_bound(wl, view, y, x, hits, flags, eps=DIR_EPS):
     nv = float(n @ v)
     F0 = 0.04 * (1.0 - m) + a * m
     seed, spp = wl.params.seed, wl.params.spp
+    z = float(wl.depth[view, y, x])
+    if not (np.isfinite(z) and z > 0):  # background: the map at mip 0 in the view direction
+        return _lookup_dev(mips, He, We, -v, eps)
     key = np.array([seed & 0xffffffff, (seed >> 32) ^ view], np.uint32)
     out = np.zeros(3)
     for s in range(spp):
-        if hits[s] != -1:
-            continue  # a hit, an invalid sample or background
+        if hits[s] < -1 or (hits[s] >= 0 and c1_diff is None):
+            continue  # an invalid sample, background, or a hit without c1 to compare
         o = O.philox4x32_10(np.array([y * W + x, s, 0, 0], np.uint32), key)
         xi0, xi1 = float(int(o[0]) >> 8) / 16777216.0, float(int(o[1]) >> 8) / 16777216.0
         h = O.ggx_sample_h(n, rho, xi0, xi1)
@@ -124,13 +136,7 @@ def direction_bound(wl, view, y, x, hits, flags, eps=DIR_EPS):
         nw = float(n @ w)
         if not (nv > 0 and nw > 0 and vh > 0 and nh > 0):
             continue
-        Li = O.env_lookup(mips, He, We, w, 0.0)
-        dev = np.zeros(3)
-        for k in range(3):
-            for sg in (1.0, -1.0):
-                w2 = w.copy()
-                w2[k] += sg * eps
-                dev = np.maximum(dev, np.abs(O.env_lookup(mips, He, We, w2 / np.linalg.norm(w2), 0.0) - Li))
+        dev = c1_diff[view].reshape(-1, 3)[hits[s]] if hits[s] >= 0 else _lookup_dev(mips, He, We, w, eps)
         K = O.ggx_G1(nw, rho) * O.ggx_G1(nv, rho) * vh / (nv * nh)
         out += (F0 + (1.0 - F0) * (1.0 - vh) ** 5) * K * dev / spp
         if flags & O.FLAG_DIFFUSE_INDIRECT:
@@ -138,6 +144,18 @@ def direction_bound(wl, view, y, x, hits, flags, eps=DIR_EPS):
             if pdf > 0 and np.isfinite(pdf):
                 out += (1.0 - m) * a / math.pi * nw / pdf * dev / spp
     return out
+
+
+def _lookup_dev(mips, He, We, d, eps):
+    """Largest change of the mip-0 lookup (per channel) when one component of d moves by +-eps."""
+    L = O.env_lookup(mips, He, We, d, 0.0)
+    dev = np.zeros(3)
+    for k in range(3):
+        for sg in (1.0, -1.0):
+            d2 = np.array(d, np.float64)
+            d2[k] += sg * eps
+            dev = np.maximum(dev, np.abs(O.env_lookup(mips, He, We, d2 / np.linalg.norm(d2), 0.0) - L))
+    return dev
 
 
 _MIPS = {}
@@ -161,6 +179,7 @@ def assert_forward_parity(gpu, orc, label="", wl=None, pix=None, flags=0):
     pix_ok = ~bad.any(axis=-1)
     scale = np.maximum(np.abs(orc["final"]).max(axis=-1), RGB_FLOOR)
     bounds = {}
+    c1_diff = np.abs(gpu["c1"].astype(np.float64) - orc["c1"]) if ("c1" in gpu and "c1" in orc) else None
     for key in [k for k in ("final", "cs_mc", "c_id") if k in gpu]:
         okey = {"c_id": "cid"}.get(key, key)
         # error of each channel in units of the pixel's output RGB
@@ -178,7 +197,8 @@ def assert_forward_parity(gpu, orc, label="", wl=None, pix=None, flags=0):
             lin = int(pix[t[0]]) if pix is not None else (t[0] * H + t[1]) * W + t[2]
             if lin not in bounds:
                 vv, rem = divmod(lin, H * W)
-                bounds[lin] = direction_bound(wl, vv, rem // W, rem % W, gpu["hit_idx"][t], flags).max()
+                bounds[lin] = direction_bound(wl, vv, rem // W, rem % W, gpu["hit_idx"][t], flags,
+                                              c1_diff=c1_diff).max()
             allowed = RGB_RTOL_MAX + bounds[lin] / scale[t]
             assert err_all[t] <= allowed, \
                 f"{label}: {key}: pixel {lin} rel err {err_all[t]:.3e} > {allowed:.3e} (conditioning bound)"

@@ -252,6 +252,22 @@ def test_config3_full_size_backward(S, olut, flags):
     _assert_backward_parity(ggpu, gorc, aff, excuse=excuse, excused_max=int(1e-5 * aff.size) + 1)
 
 
+def test_config4_eight_views_full_size_step():
+    """Config 4 (8 views of 1245x825 around one scene, 32 spp, 512x1024 map: the fused step's
+    workload) through the per-stage path, every pixel of every view and every texel against the
+    oracle's forward and adjoint, under the same rules as config 3.  The fused step equals this
+    path bit for bit in final and hit indices (test_gpu_fused)."""
+    import paper_2504_01358_gb300 as S
+    wl = si.config4()
+    olut = O.build_lut()
+    fw = {}
+    ggpu, gorc, aff = _backward_pair(S, wl, olut, 0, forward_out=fw)
+    assert_forward_parity(fw["gpu"], fw["orc"], "config4", wl=wl, flags=0)
+    assert aff.mean() < 0.01, float(aff.mean())
+    excuse = forward_outliers(fw["gpu"], fw["orc"]) | direct_kinks(wl)
+    _assert_backward_parity(ggpu, gorc, aff, excuse=excuse, excused_max=int(1e-5 * aff.size) + 1)
+
+
 @pytest.mark.parametrize("flags", [0, 1])
 @pytest.mark.parametrize("name", ["small", "cfg1"])
 def test_pathwise_backward_matches_oracle_adjoint(S, olut, request, name, flags):
