@@ -1,0 +1,49 @@
+"""Host-side pieces of bench.py that need no GPU: the committed ncu summaries it reads for the
+roofline (parsed, keyed by a hash of the kernel sources, ignored once the sources change) and the
+ALU roofline arithmetic."""
+import os
+import shutil
+
+import pytest
+
+import bench
+
+
+def test_trace_profile_summary_is_parsed_and_keyed_by_the_sources(tmp_path):
+    path = bench.TRACE_PROFILE
+    assert os.path.exists(path), "the trace's ncu summary is committed under profiles/"
+    text = open(path).read()
+    assert "--clock-control none" in text  # the command that made it is recorded
+    kv = bench.profile_summary()
+    if kv is None:
+        pytest.skip("the trace sources changed since the summary was captured (bench reports null)")
+    for key in ("dram_bytes_per_launch", "lts_bytes_per_launch", "warp_execution_efficiency", "alu_pipe_pct",
+                "issue_active_pct", "duration_ms"):
+        assert bench.profiled(kv, key) is not None, key
+    assert 0.0 < bench.profiled(kv, "warp_execution_efficiency") <= 1.0
+    assert 0.0 < bench.profiled(kv, "alu_pipe_pct") <= 100.0
+    # the same summary under another file list (other sources) is not used
+    assert bench.profile_summary(path, files=("k_prep.cu",)) is None
+    # a summary whose hash line is altered is not used either
+    alt = tmp_path / "alt.txt"
+    shutil.copy(path, alt)
+    lines = alt.read_text().splitlines()
+    lines = [("kernel_source_sha256_16: 0000000000000000" if ln.startswith("kernel_source_sha256_16") else ln)
+             for ln in lines]
+    alt.write_text("\n".join(lines) + "\n")
+    assert bench.profile_summary(str(alt)) is None
+    assert bench.profile_summary(str(tmp_path / "missing.txt")) is None
+
+
+def test_profiled_tolerates_missing_and_malformed_values():
+    assert bench.profiled(None, "x") is None
+    assert bench.profiled({"x": "n/a"}, "x") is None
+    assert bench.profiled({"x": "1.5"}, "y") is None
+    assert bench.profiled({"x": "1.5"}, "x") == 1.5
+
+
+def test_whole_job_rate_and_alu_peak_arithmetic():
+    # 152 SMs x 128 FP32 lanes x 2070 MHz = 40.27 Tops/s, the roofline's derived ALU peak
+    assert bench.SM_COUNT * bench.FP32_LANES_PER_SM * 2070.0 * 1e6 / 1e9 == pytest.approx(40273.92)
+    # one rank, 23.04 M rays in 3.2 ms
+    assert bench.whole_job_rate(23040000.0, 1, 3.2) == pytest.approx(7.2e9)
