@@ -81,11 +81,11 @@ __device__ __forceinline__ float2 sample_uniforms(uint64_t seed, int view, uint3
 // ------------------------------------------------------------------------------------------
 // Microfacet terms (Appendix B); alpha = rho as printed.
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ float ggx_D(float nh, float rho) {
-  const float a2 = rho * rho;
-  const float den = nh * nh * (a2 - 1.0f) + 1.0f;
-  return a2 / (kPi * den * den);
-}
+// D at a half vector drawn by ggx_sample_h with denominator ds: there
+// 1 + (n.h)^2 (rho^2 - 1) = rho^2 / ds exactly, so D = ds^2 / (pi rho^2), free of the
+// cancellation that 1 + (n.h)^2 (rho^2 - 1) suffers for n.h -> 1 at low roughness (n.h
+// rounded to FP32 near 1 has lost most of the information that sin(theta_h) keeps).
+__device__ __forceinline__ float ggx_D_sampled(float ds, float rho) { return ds * ds / (kPi * (rho * rho)); }
 __device__ __forceinline__ float ggx_G1(float z, float rho) {
   const float a2 = rho * rho;
   return 2.0f * z / (z + sqrtf(a2 + (1.0f - a2) * z * z));
@@ -99,17 +99,19 @@ __device__ __forceinline__ float f0_of(float a, float m) { return 0.04f * (1.0f 
 // GGX half vector around n (Walter et al. 2007 inversion; frame of Duff et al. 2017).
 // cos^2 = (1 - xi0) / den and sin^2 = rho^2 xi0 / den with den = 1 + (rho^2 - 1) xi0: the
 // same values as sqrt(1 - cos^2) without its cancellation for near-mirror lobes.  *ct
-// receives cos(theta_h) = n.h.
-// den = 1 + (rho^2 - 1) xi0 is formed as (1 - xi0) + rho^2 xi0: the same number without the
-// cancellation of the first form as xi0 -> 1 (1 - xi0 is exact on the uniforms' 2^-24 grid), so
-// that cos^2 + sin^2 stays 1 to a few ulp and h stays a unit vector; with the first form a
+// receives cos(theta_h) = n.h and *den_out den.
+// den is formed as (1 - xi0) + rho^2 xi0: the same number without the cancellation of the
+// first form as xi0 -> 1 (1 - xi0 is exact on the uniforms' 2^-24 grid), so that
+// cos^2 + sin^2 stays 1 to a few ulp and h stays a unit vector; with the first form a
 // low-roughness sample's h could be ~1e-5 too long, turning its reflection by as much.
-__device__ __forceinline__ float3 ggx_sample_h(float3 n, float rho, float xi0, float xi1, float* ct_out = nullptr) {
+__device__ __forceinline__ float3 ggx_sample_h(float3 n, float rho, float xi0, float xi1, float* ct_out = nullptr,
+                                               float* den_out = nullptr) {
   const float a2 = rho * rho;
   const float den = fmaf(a2, xi0, 1.0f - xi0);
   const float ct = sqrtf((1.0f - xi0) / den);
   const float st = sqrtf(a2 * xi0 / den);
   if (ct_out) *ct_out = ct;
+  if (den_out) *den_out = den;
   float sp, cp;
   sincospif(2.0f * xi1, &sp, &cp);
   const float sgn = n.z >= 0.0f ? 1.0f : -1.0f;
@@ -149,6 +151,7 @@ __device__ __forceinline__ void ggx_sample_h_jac(float3 n, float rho, float xi0,
 struct Sample {
   float3 h, w;
   float vh, nh, nw;
+  float ds;  // the sampler's denominator (1 - xi0) + rho^2 xi0 (ggx_D_sampled)
   bool valid;
 };
 
@@ -156,7 +159,7 @@ struct Sample {
 // both better conditioned in FP32 than dot products with the rounded vectors.
 __device__ __forceinline__ Sample make_sample(float3 n, float3 v, float nv, float rho, float2 xi) {
   Sample s;
-  s.h = ggx_sample_h(n, rho, xi.x, xi.y, &s.nh);
+  s.h = ggx_sample_h(n, rho, xi.x, xi.y, &s.nh, &s.ds);
   s.vh = dot3(v, s.h);
   s.w = s.h * (2.0f * s.vh) - v;
   s.nw = fmaf(2.0f * s.vh, s.nh, -nv);

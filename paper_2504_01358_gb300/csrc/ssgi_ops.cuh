@@ -428,7 +428,7 @@ __device__ __forceinline__ float3 trace_pixel(const FrameArgs& A, int x, int y, 
       const float3 F = F0 + (f3(1.f, 1.f, 1.f) - F0) * fc;
       acc = acc + mul3(F, Li) * K;
       if (kCid) {
-        const float pdf = ggx_D(sm.nh, rho) * sm.nh / (4.0f * sm.vh);
+        const float pdf = ggx_D_sampled(sm.ds, rho) * sm.nh / (4.0f * sm.vh);
         if (pdf > 0.0f && isfinite(pdf)) accd = accd + mul3(a, Li) * ((1.0f - m) * kInvPi * sm.nw / pdf);
       }
     }
@@ -490,12 +490,13 @@ __device__ __forceinline__ void dlnG1(float z, float rho, float& dz, float& dr) 
   dr = -(rho * (1.0f - z * z) / s) / (z + s);
 }
 
-// d ln D(c; rho) / dc, / drho with c = n.h
-__device__ __forceinline__ void dlnD(float c, float rho, float& dc, float& dr) {
-  const float a2 = rho * rho;
-  const float den = c * c * (a2 - 1.0f) + 1.0f;
-  dc = -4.0f * c * (a2 - 1.0f) / den;
-  dr = 2.0f / rho - 4.0f * rho * c * c / den;
+// d ln D(c; rho) / dc, / drho with c = n.h, at a half vector drawn by ggx_sample_h with
+// denominator ds (1 + c^2 (rho^2 - 1) = rho^2 / ds there, see ggx_D_sampled):
+//   dc = -4 c (rho^2 - 1) / (1 + c^2 (rho^2 - 1)),  dr = 2 / rho - 4 rho c^2 / (1 + c^2 (rho^2 - 1)).
+__device__ __forceinline__ void dlnD(float c, float ds, float rho, float& dc, float& dr) {
+  const float q = ds / (rho * rho);  // 1 / (1 + c^2 (rho^2 - 1))
+  dc = 4.0f * c * (1.0f - rho * rho) * q;
+  dr = 2.0f / rho - 4.0f * rho * c * c * q;
 }
 
 // Scatter g (per channel) with weight `scale` through the bilinear taps into gm, and return
@@ -612,7 +613,7 @@ __device__ __forceinline__ void bwd_mc_pixel(const FrameArgs& A, long long p) {
       float dgw_z, dgw_r;
       dlnG1(sm.nw, rho, dgw_z, dgw_r);
       float dd_c = 0.0f, dd_r = 0.0f;
-      if (rho > 0.0f) dlnD(sm.nh, rho, dd_c, dd_r);
+      if (rho > 0.0f) dlnD(sm.nh, sm.ds, rho, dd_c, dd_r);
       if (!kPathwise) {
         float dlnK_r = dgw_r + dgv_r;
         float3 dlnK_n = sm.w * dgw_z + v * (dgv_z - 1.0f / nv);
@@ -625,7 +626,7 @@ __device__ __forceinline__ void bwd_mc_pixel(const FrameArgs& A, long long p) {
       }
       float gcid = 0.0f;  // d loss / d ln(n.w / pdf) of the diffuse-indirect summand
       if (want_cid) {
-        const float pdf = ggx_D(sm.nh, rho) * sm.nh / (4.0f * sm.vh);
+        const float pdf = ggx_D_sampled(sm.ds, rho) * sm.nh / (4.0f * sm.vh);
         if (pdf > 0.0f && isfinite(pdf)) {
           const float kk = kInvPi / pdf;
           ga = ga + mul3(gC, Li) * ((1.0f - m) * kk * sm.nw);
