@@ -233,6 +233,12 @@ ssgi_status ssgi_step_fused(const ssgi_gbuffer *g, const ssgi_camera *cams, cons
                             void *workspace, size_t ws_bytes, ssgi_stream_t stream);
 /* Synchronous: *failed = 1 if the last fused step on this workspace stopped at a barrier. */
 ssgi_status ssgi_step_fused_check(const void *workspace, int32_t *failed);
+/* How long a block of later ssgi_step_fused launches waits at a grid barrier before it gives
+ * up: `polls` polls of ~100 ns each; a negative value restores the default (2^26 polls, several
+ * seconds).  Process-wide, read at each launch.  A short limit makes the step stop at its first
+ * barrier with ssgi_step_fused_check reporting failure, as a stalled block would (a test of
+ * the error path: the blocks return, nothing faults, and the next launch starts clean). */
+ssgi_status ssgi_step_fused_set_wait_limit(int64_t polls);
 /* Synchronous: the durations (ns, from %globaltimer) of the last fused step's phases as seen by
  * its first block, in order: pyramids (env mips + Hi-Z, with the clears), direct shading,
  * trace + loss, Monte-Carlo adjoint, direct adjoint, mip-chain adjoint (the last is block 0's
@@ -326,8 +332,9 @@ size_t ssgi_serve_request_bytes(ssgi_dims d, int32_t env_h, int32_t env_w, int32
  * workspace it uses a scratch array of SSGI_BACKWARD_NOALLOC_MAX_BYTES that lives in the
  * library's device image: every GPU that loads the library keeps that memory until the process
  * exits.  It calls no cudaMalloc or cudaFree and no allocating library routine.
- *   - The first call on a device looks up that device's address of the array (with that device
- *     current); make that first call before any stream capture.
+ *   - Every call looks up the array's device address with the caller's device current (no
+ *     cached address outlives a cudaDeviceReset); the first call on a device also loads the
+ *     library's module there, so make that first call before any stream capture.
  *   - Sizes whose workspace (ssgi_backward_workspace_bytes) exceeds the maximum return
  *     SSGI_ERR_UNSUPPORTED before anything is enqueued.
  *   - The scratch is cleared on `stream` at the start of every call and keeps the last call's

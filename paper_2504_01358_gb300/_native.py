@@ -102,6 +102,7 @@ _SIGS = {
     "ssgi_step_fused": (C.c_int, [C.POINTER(GBuffer), C.POINTER(Camera), VP, I32, I32, VP, I32, VP,
                                   C.POINTER(TraceParams), VP, VP, VP, VP, VP, VP, VP, VP, VP, SZ, VP]),
     "ssgi_step_fused_check": (C.c_int, [VP, C.POINTER(I32)]),
+    "ssgi_step_fused_set_wait_limit": (C.c_int, [I64]),
     "ssgi_step_fused_phase_ns": (C.c_int, [VP, C.POINTER(C.c_uint64)]),
     "ssgi_read_bandwidth_probe": (C.c_int, [VP, SZ, I32, VP, VP]),
     "ssgi_depth_normals": (C.c_int, [VP, Dims, C.POINTER(Camera), VP, VP]),

@@ -13,6 +13,7 @@
 // The per-item code is the stand-alone kernels' (ssgi_ops.cuh), so the results match the
 // per-stage path bit for bit (gradients up to the order of atomic additions).
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 
 #include "ssgi_ops.cuh"
@@ -20,7 +21,7 @@
 namespace ssgi {
 
 constexpr int kFusedThreads = 128;                // one 8 x 16 trace tile per block iteration
-constexpr long long kBarrierSpinLimit = 1ll << 26;  // x ~100 ns sleeps: several seconds
+constexpr long long kBarrierSpinLimit = 1ll << 26;  // x ~100 ns sleeps: several seconds (default)
 constexpr int kFusedBarBytes = 512;               // control block at the start of the workspace
 constexpr int kFusedStampOffset = 256;            // bytes into it: 64-bit phase timestamps
 
@@ -49,6 +50,7 @@ struct FusedArgs {
   unsigned* ctl;     // workspace: control block
   long long n_gc1;   // float4s of g_c1
   int n_gmips;       // float4s of g_mips
+  long long wait_limit;  // polls a block makes at a grid barrier before it gives up
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -91,8 +93,9 @@ __device__ __forceinline__ bool last_arrival(unsigned* counter, unsigned total) 
   return last;
 }
 
-// Grid barrier for a cooperative launch; returns false if any block gave up waiting.
-__device__ __forceinline__ bool grid_sync(unsigned* ctl) {
+// Grid barrier for a cooperative launch; returns false if any block gave up waiting (after
+// `limit` polls of ~100 ns each).
+__device__ __forceinline__ bool grid_sync(unsigned* ctl, long long limit) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -113,7 +116,7 @@ __device__ __forceinline__ bool grid_sync(unsigned* ctl) {
           ok = 0;
           break;
         }
-        if (++spins > kBarrierSpinLimit) {
+        if (++spins > limit) {
           atomicExch(const_cast<unsigned*>(verr), 1u);
           ok = 0;
           break;
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(kFusedThreads, 7) k_step_fused(const __grid_co
       }
     });
   }
-  if (!grid_sync(F.ctl)) return;
+  if (!grid_sync(F.ctl, F.wait_limit)) return;
   stamp(F.ctl, 1);
 
   // P1: direct shading
@@ -188,7 +191,7 @@ __global__ void __launch_bounds__(kFusedThreads, 7) k_step_fused(const __grid_co
     const long long npx = s_k.npx, gsz = s_k.gsz;
     for (long long p = (long long)blockIdx.x * kFusedThreads + threadIdx.x; p < npx; p += gsz) shade_pixel(A, p);
   }
-  if (!grid_sync(F.ctl)) return;
+  if (!grid_sync(F.ctl, F.wait_limit)) return;
   stamp(F.ctl, 2);
 
   // P2: trace, one 8 x 16 tile per block iteration, and the L2 loss of each finished pixel.
@@ -211,7 +214,7 @@ __global__ void __launch_bounds__(kFusedThreads, 7) k_step_fused(const __grid_co
     });
     block_sum_add(acc, F.loss, 1.0f / (float)(s_k.npx * 3));
   }
-  if (!grid_sync(F.ctl)) return;
+  if (!grid_sync(F.ctl, F.wait_limit)) return;
   stamp(F.ctl, 3);
 
   // P3: Monte-Carlo adjoint (scatters into g_c1 and g_mips)
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(kFusedThreads, 7) k_step_fused(const __grid_co
     const long long p = (long long)c * kFusedThreads + threadIdx.x;
     if (p < s_k.npx) bwd_mc_pixel<kPathwise>(A, p);
   });
-  if (!grid_sync(F.ctl)) return;
+  if (!grid_sync(F.ctl, F.wait_limit)) return;
   stamp(F.ctl, 4);
 
   // P4: direct-shading adjoint
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(kFusedThreads, 7) k_step_fused(const __grid_co
     const long long p = (long long)c * kFusedThreads + threadIdx.x;
     if (p < s_k.npx) bwd_direct_pixel(A, p);
   });
-  if (!grid_sync(F.ctl)) return;
+  if (!grid_sync(F.ctl, F.wait_limit)) return;
   stamp(F.ctl, 5);
 
   // P5: mip-chain adjoint to the base texels
@@ -261,11 +264,19 @@ inline FusedLayout fused_layout(ssgi_dims d, int env_h, int env_w, int levels) {
   return L;
 }
 
+// Polls a block makes at a grid barrier before it gives up; negative = kBarrierSpinLimit.
+std::atomic<long long> g_wait_limit{-1};
+
 }  // namespace ssgi
 
 using namespace ssgi;
 
 extern "C" {
+
+ssgi_status ssgi_step_fused_set_wait_limit(int64_t polls) {
+  g_wait_limit.store(polls < 0 ? -1 : (long long)polls);
+  return SSGI_OK;
+}
 
 size_t ssgi_step_fused_workspace_bytes(ssgi_dims d, int32_t env_h, int32_t env_w, int32_t hiz_levels) {
   if (!dims_ok(d) || ssgi_env_levels(env_h, env_w) < 1 || hiz_levels < 1 || hiz_levels > SSGI_MAX_HIZ_LEVELS) return 0;
@@ -301,6 +312,8 @@ ssgi_status ssgi_step_fused(const ssgi_gbuffer* g, const ssgi_camera* cams, cons
   F.ctl = (unsigned*)(ws + L.bar);
   F.n_gc1 = npx;
   F.n_gmips = (int)(ssgi_env_mip_floats(env_h, env_w) / 3);
+  const long long lim = g_wait_limit.load();
+  F.wait_limit = lim < 0 ? kBarrierSpinLimit : lim;
   A.depth = g->depth;
   A.normal = g->normal;
   A.albedo = g->albedo;

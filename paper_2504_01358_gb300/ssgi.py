@@ -280,6 +280,11 @@ def ssgi_step_fused_check(workspace: torch.Tensor) -> bool:
     return bool(f.value)
 
 
+def ssgi_step_fused_set_wait_limit(polls: int) -> None:
+    """Polls (~100 ns each) a fused-step block waits at a grid barrier before giving up; < 0: default."""
+    N.call("ssgi_step_fused_set_wait_limit", int(polls))
+
+
 FUSED_PHASES = ("pyramids", "shade", "trace_loss", "bwd_mc", "bwd_direct", "bwd_env")
 
 

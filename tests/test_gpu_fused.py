@@ -82,3 +82,28 @@ def test_config4_eight_views_fused_against_per_stage_and_oracle():
     sub = {"hit_idx": got["hit_idx"].reshape(V * H * W, -1)[pl], "final": got["final"].reshape(-1, 3)[pl]}
     assert_forward_parity(sub, r, "config4 sample")
     assert (sub["hit_idx"] >= 0).mean() > 0.02
+
+
+def test_fused_barrier_gives_up_and_the_next_step_is_clean():
+    """The grid barrier's bounded wait: with the wait limit at 0 polls a block that reaches a
+    barrier before the others gives up at once, marks the error word and every block returns
+    (no hang, no fault); ssgi_step_fused_check reports it.  With the default limit restored the
+    next launch on the same workspace runs to the end and equals the per-stage path."""
+    import paper_2504_01358_gb300 as S
+    wl = si.small_case()
+    lut = S.ssgi_build_brdf_lut()
+    g, env, cams, tgt = S.to_device_workload(wl)
+    p = S.params_of(wl.params)
+    try:
+        S.ssgi_step_fused_set_wait_limit(0)
+        out = S.ssgi_step_fused(g, cams, env, lut, tgt, p)
+        torch.cuda.synchronize()
+        assert S.ssgi_step_fused_check(out["_workspace"])
+    finally:
+        S.ssgi_step_fused_set_wait_limit(-1)
+    out = S.ssgi_step_fused(g, cams, env, lut, tgt, p, out=out, workspace=out["_workspace"])
+    torch.cuda.synchronize()
+    assert not S.ssgi_step_fused_check(out["_workspace"])
+    got = {k: v.cpu().numpy() for k, v in out.items() if k != "_workspace"}
+    got["loss"] = float(got["loss"][0])
+    _compare(got, _per_stage(S, wl, lut))
