@@ -26,7 +26,10 @@ __device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x 
 __device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
 __device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(a.x * s, a.y * s, a.z * s); }
 __device__ __forceinline__ float3 mul3(float3 a, float3 b) { return f3(a.x * b.x, a.y * b.y, a.z * b.z); }
-__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+// x y z order, one rounding per step (never re-fused by the compiler)
+__device__ __forceinline__ float dot3(float3 a, float3 b) {
+  return __fmaf_rn(a.z, b.z, __fmaf_rn(a.y, b.y, __fmul_rn(a.x, b.x)));
+}
 __device__ __forceinline__ float3 ld3(const float* __restrict__ p) { return f3(__ldg(p), __ldg(p + 1), __ldg(p + 2)); }
 __device__ __forceinline__ void st3(float* p, float3 v) { p[0] = v.x; p[1] = v.y; p[2] = v.z; }
 __device__ __forceinline__ float comp(float3 v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : v.z); }
@@ -45,15 +48,75 @@ __device__ __forceinline__ float3 cam_to_world(const DevCam& c, float3 d) {
 // World-space direction through the centre of pixel (x, y) (camera-space forward component 1;
 // the -1 z term is exact, so each component takes two roundings).
 __device__ __forceinline__ float3 pix_dir_world(const DevCam& c, int x, int y) {
-  const float dx = ((float)x + 0.5f - c.cx) / c.f, dy = -((float)y + 0.5f - c.cy) / c.f;
+  // the numerators are exact (half-integers); one rounding in each quotient
+  const float dx = __fdiv_rn((float)x + 0.5f - c.cx, c.f), dy = -__fdiv_rn((float)y + 0.5f - c.cy, c.f);
   return f3(fmaf(c.R[0], dx, fmaf(c.R[1], dy, -c.R[2])), fmaf(c.R[3], dx, fmaf(c.R[4], dy, -c.R[5])),
             fmaf(c.R[6], dx, fmaf(c.R[7], dy, -c.R[8])));
+}
+// Unit vector from the surface point of a pixel to the camera: -d / |d| for the pixel's ray d.
+__device__ __forceinline__ float3 view_vector(float3 d) {
+  const float s = __fdiv_rn(-1.0f, __fsqrt_rn(dot3(d, d)));
+  return f3(__fmul_rn(d.x, s), __fmul_rn(d.y, s), __fmul_rn(d.z, s));
+}
+// Mirror direction r = 2 (v.n) n - v.
+__device__ __forceinline__ float3 reflect_about(float3 n, float nv, float3 v) {
+  const float t = 2.0f * nv;  // exact
+  return f3(__fmaf_rn(n.x, t, -v.x), __fmaf_rn(n.y, t, -v.y), __fmaf_rn(n.z, t, -v.z));
 }
 __device__ __forceinline__ float3 world_to_cam(const DevCam& c, float3 d) {
   return f3(c.R[0] * d.x + c.R[3] * d.y + c.R[6] * d.z, c.R[1] * d.x + c.R[4] * d.y + c.R[7] * d.z,
             c.R[2] * d.x + c.R[5] * d.y + c.R[8] * d.z);
 }
 __device__ __forceinline__ bool is_background(float z) { return !(isfinite(z) && z > 0.0f); }
+
+// ------------------------------------------------------------------------------------------
+// sin(pi x), cos(pi x) and atan(num / den) in FP32 with explicitly rounded steps, so that the
+// sampled directions and the environment-map coordinates are the same bits wherever this
+// arithmetic is replayed.  sin/cos: exact reduction to the nearest quarter turn k/2 (2x and
+// x - k/2 are exact), then the Taylor series of sin(pi f) and cos(pi f) on |f| <= 1/4 through
+// f^9 and f^10 (truncation below 2e-9).  atan: for |t| > tan(pi/8) the identity
+// atan(t) = pi/4 + atan((t - 1)/(t + 1)) brings the argument to |r| <= tan(pi/8), where the
+// alternating series through r^15 is within 2e-8.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void sincospi_rn(float x, float* s, float* c) {
+  const float k = rintf(2.0f * x);
+  const float f = __fmaf_rn(k, -0.5f, x);
+  const float f2 = __fmul_rn(f, f);
+  float ps = __fmaf_rn(f2, 8.2145886611128190e-02f, -5.9926452932079207e-01f);  // pi^9/9!, -pi^7/7!
+  ps = __fmaf_rn(ps, f2, 2.5501640398773455e+00f);                               // pi^5/5!
+  ps = __fmaf_rn(ps, f2, -5.1677127800499703e+00f);                              // -pi^3/3!
+  ps = __fmaf_rn(ps, f2, 3.1415926535897932e+00f);                               // pi
+  ps = __fmul_rn(ps, f);
+  float pc = __fmaf_rn(f2, -2.5806891390014061e-02f, 2.3533063035889320e-01f);  // -pi^10/10!, pi^8/8!
+  pc = __fmaf_rn(pc, f2, -1.3352627688545895e+00f);                               // -pi^6/6!
+  pc = __fmaf_rn(pc, f2, 4.0587121264167682e+00f);                                // pi^4/4!
+  pc = __fmaf_rn(pc, f2, -4.9348022005446793e+00f);                               // -pi^2/2!
+  pc = __fmaf_rn(pc, f2, 1.0f);
+  const int q = ((int)k) & 3;
+  *s = q == 0 ? ps : (q == 1 ? pc : (q == 2 ? -ps : -pc));
+  *c = q == 0 ? pc : (q == 1 ? -ps : (q == 2 ? -pc : ps));
+}
+
+// atan(num / den) for |num| <= den (an octant-reduced angle, in [-pi/4, pi/4]).  With den = 0
+// (and so num = 0: a direction along the map's axis) the signed zeros decide as in atan2:
+// +-0 for den = +0, +-pi for den = -0.
+__device__ __forceinline__ float atan_octant_rn(float num, float den) {
+  if (den == 0.0f) return copysignf(signbit(den) ? kPi : 0.0f, num);
+  const float an = fabsf(num);
+  const bool big = an > __fmul_rn(0.41421356237309505f, den);
+  // one division: the reduced argument's numerator and denominator are selected first
+  const float r = __fdiv_rn(big ? __fsub_rn(an, den) : an, big ? __fadd_rn(an, den) : den);
+  const float r2 = __fmul_rn(r, r);
+  float p = __fmaf_rn(r2, -1.0f / 15.0f, 1.0f / 13.0f);
+  p = __fmaf_rn(p, r2, -1.0f / 11.0f);
+  p = __fmaf_rn(p, r2, 1.0f / 9.0f);
+  p = __fmaf_rn(p, r2, -1.0f / 7.0f);
+  p = __fmaf_rn(p, r2, 1.0f / 5.0f);
+  p = __fmaf_rn(p, r2, -1.0f / 3.0f);
+  const float at = __fmaf_rn(__fmul_rn(r, r2), p, r);
+  const float a = big ? __fadd_rn(0.78539816339744831f, at) : at;
+  return num < 0.0f ? -a : a;
+}
 
 // ------------------------------------------------------------------------------------------
 // Philox4x32-10: ten rounds of the 4x32 S-box, multipliers 0xD2511F53 / 0xCD9E8D57 and key
@@ -106,20 +169,24 @@ __device__ __forceinline__ float f0_of(float a, float m) { return 0.04f * (1.0f 
 // low-roughness sample's h could be ~1e-5 too long, turning its reflection by as much.
 __device__ __forceinline__ float3 ggx_sample_h(float3 n, float rho, float xi0, float xi1, float* ct_out = nullptr,
                                                float* den_out = nullptr) {
-  const float a2 = rho * rho;
-  const float den = fmaf(a2, xi0, 1.0f - xi0);
-  const float ct = sqrtf((1.0f - xi0) / den);
-  const float st = sqrtf(a2 * xi0 / den);
+  const float a2 = __fmul_rn(rho, rho);
+  const float om = 1.0f - xi0;  // exact on the 2^-24 grid
+  const float den = __fmaf_rn(a2, xi0, om);
+  const float ct = __fsqrt_rn(__fdiv_rn(om, den));
+  const float st = __fsqrt_rn(__fdiv_rn(__fmul_rn(a2, xi0), den));
   if (ct_out) *ct_out = ct;
   if (den_out) *den_out = den;
   float sp, cp;
-  sincospif(2.0f * xi1, &sp, &cp);
+  sincospi_rn(2.0f * xi1, &sp, &cp);
   const float sgn = n.z >= 0.0f ? 1.0f : -1.0f;
-  const float aa = -1.0f / (sgn + n.z);
-  const float bb = n.x * n.y * aa;
-  const float3 t1 = f3(1.0f + sgn * n.x * n.x * aa, sgn * bb, -sgn * n.x);
-  const float3 t2 = f3(bb, sgn + n.y * n.y * aa, -n.y);
-  return t1 * (st * cp) + t2 * (st * sp) + n * ct;
+  const float aa = __fdiv_rn(-1.0f, __fadd_rn(sgn, n.z));
+  const float bb = __fmul_rn(__fmul_rn(n.x, n.y), aa);
+  const float3 t1 = f3(__fmaf_rn(__fmul_rn(sgn * n.x, n.x), aa, 1.0f), sgn * bb, -sgn * n.x);
+  const float3 t2 = f3(bb, __fmaf_rn(__fmul_rn(n.y, n.y), aa, sgn), -n.y);
+  const float c1 = __fmul_rn(st, cp), c2 = __fmul_rn(st, sp);
+  return f3(__fmaf_rn(n.x, ct, __fmaf_rn(t2.x, c2, __fmul_rn(t1.x, c1))),
+            __fmaf_rn(n.y, ct, __fmaf_rn(t2.y, c2, __fmul_rn(t1.y, c1))),
+            __fmaf_rn(n.z, ct, __fmaf_rn(t2.z, c2, __fmul_rn(t1.z, c1))));
 }
 
 // Derivatives of ggx_sample_h's half vector at fixed uniforms with respect to n.x, n.y, n.z
@@ -133,7 +200,7 @@ __device__ __forceinline__ void ggx_sample_h_jac(float3 n, float rho, float xi0,
   const float q = sqrtf(xi0 / den);
   const float st = rho * q;
   float sp, cp;
-  sincospif(2.0f * xi1, &sp, &cp);
+  sincospi_rn(2.0f * xi1, &sp, &cp);
   const float sgn = n.z >= 0.0f ? 1.0f : -1.0f;
   const float aa = -1.0f / (sgn + n.z);
   const float aa2 = aa * aa;
@@ -161,7 +228,7 @@ __device__ __forceinline__ Sample make_sample(float3 n, float3 v, float nv, floa
   Sample s;
   s.h = ggx_sample_h(n, rho, xi.x, xi.y, &s.nh, &s.ds);
   s.vh = dot3(v, s.h);
-  s.w = s.h * (2.0f * s.vh) - v;
+  s.w = reflect_about(s.h, s.vh, v);
   s.nw = fmaf(2.0f * s.vh, s.nh, -nv);
   s.valid = (nv > 0.0f) && (s.nw > 0.0f) && (s.vh > 0.0f) && (s.nh > 0.0f);
   return s;
@@ -170,12 +237,6 @@ __device__ __forceinline__ Sample make_sample(float3 n, float3 v, float nv, floa
 // ------------------------------------------------------------------------------------------
 // Environment lookup
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ float2 dir_to_uv(float3 d) {
-  const float u = 0.5f + atan2f(d.x, -d.z) * kInv2Pi;
-  const float v = atan2f(sqrtf(d.x * d.x + d.z * d.z), d.y) * kInvPi;
-  return make_float2(u, v);
-}
-
 struct Taps {
   int idx[4];  // float offsets of the four texels
   float tx, ty;
@@ -184,7 +245,8 @@ struct Taps {
 // Octant-reduced angles of a direction: the texel coordinates x = u w - 0.5 and y = v h - 0.5
 // of the lat-long mapping are written as base + ang * scale with |ang| <= pi/4 and an exact
 // base, so the bilinear fractions keep full FP32 precision (a full-range atan2 near +-pi would
-// cost ~4e-5 texel at w = 512).  Same mapping as dir_to_uv.
+// cost ~4e-5 texel at w = 512).  The mapping is u = 0.5 + atan2(x, -z) / (2 pi) and
+// v = atan2(sqrt(x^2 + z^2), y) / pi.
 struct DirAngles {
   float ax, bx;  // x = bx + ax * w / (2 pi)
   float ay, by;  // y = by + ay * h / pi  (by in units of h: 0, 1/2 or 1)
@@ -192,35 +254,35 @@ struct DirAngles {
 
 __device__ __forceinline__ DirAngles dir_angles(float3 d) {
   DirAngles r;
-  // azimuth: pick the octant-reduced (numerator, denominator) pair with selects, one atan2f
+  // azimuth: pick the octant-reduced (numerator, denominator) pair with selects, one arctangent
   const float X = -d.z, Y = d.x;
   const float aX = fabsf(X), aY = fabsf(Y);
   const bool xa = aY <= X, xb = Y > aX, xc = -X >= aY;
   const float num = xa ? Y : (xb ? -X : (xc ? -Y : X));
   const float den = xa ? X : (xb ? Y : (xc ? -X : -Y));
   r.bx = xa ? 0.5f : (xb ? 0.75f : (xc ? 1.0f : 0.25f));
-  r.ax = atan2f(num, den);
+  r.ax = atan_octant_rn(num, den);
   // polar angle from +y, likewise
-  const float q = sqrtf(d.x * d.x + d.z * d.z);
+  const float q = __fsqrt_rn(__fmaf_rn(d.z, d.z, __fmul_rn(d.x, d.x)));
   const bool ya = d.y >= q, yb = -d.y >= q;
   const float ny = ya ? q : (yb ? q : d.y);
   const float dy = ya ? d.y : (yb ? -d.y : q);
   const float sg = (ya ? 1.0f : -1.0f);
   r.by = ya ? 0.0f : (yb ? 1.0f : 0.5f);
-  r.ay = sg * atan2f(ny, dy);
+  r.ay = sg * atan_octant_rn(ny, dy);
   return r;
 }
 
 // integer part and fraction of base * n - 0.5 + ang * k
 __device__ __forceinline__ void split_coord(float base, float ang, int n, float k, int& i0, float& t) {
-  const float b = fmaf(base, (float)n, -0.5f);  // exact: n is a power of two
-  float f0 = floorf(fmaf(ang, k, b));
-  t = fmaf(ang, k, b - f0);
+  const float b = __fmaf_rn(base, (float)n, -0.5f);  // exact: n is a power of two
+  float f0 = floorf(__fmaf_rn(ang, k, b));
+  t = __fmaf_rn(ang, k, __fsub_rn(b, f0));
   if (t < 0.0f) {
-    t += 1.0f;
+    t = __fadd_rn(t, 1.0f);
     f0 -= 1.0f;
   } else if (t >= 1.0f) {
-    t -= 1.0f;
+    t = __fsub_rn(t, 1.0f);
     f0 += 1.0f;
   }
   i0 = (int)f0;
@@ -230,8 +292,8 @@ __device__ __forceinline__ Taps env_taps(const EnvInfo& e, int l, const DirAngle
   Taps t;
   const int h = e.h[l], w = e.w[l];
   int x0, y0;
-  split_coord(a.bx, a.ax, w, (float)w * kInv2Pi, x0, t.tx);
-  split_coord(a.by, a.ay, h, (float)h * kInvPi, y0, t.ty);
+  split_coord(a.bx, a.ax, w, __fmul_rn((float)w, kInv2Pi), x0, t.tx);
+  split_coord(a.by, a.ay, h, __fmul_rn((float)h, kInvPi), y0, t.ty);
   int c0 = x0 % w;
   if (c0 < 0) c0 += w;
   int c1 = c0 + 1;

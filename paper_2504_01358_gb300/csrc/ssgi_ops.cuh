@@ -209,11 +209,11 @@ __device__ __forceinline__ void shade_pixel(const FrameArgs& A, long long p) {
   if (is_background(z)) {
     o1 = env_lookup0(A.mips, e, d);
   } else {
-    const float3 v = d * (-1.0f / sqrtf(dot3(d, d)));
+    const float3 v = view_vector(d);
     const float3 n = ld3(A.normal + 3 * p);
     const float nv = dot3(n, v);
     const float mu = fminf(fmaxf(nv, 1e-4f), 1.0f);
-    const float3 r = n * (2.0f * nv) - v;
+    const float3 r = reflect_about(n, nv, v);
     const float rho = __ldg(A.rough + p), m = __ldg(A.metal + p);
     const float lam = log2f(rho + 1.0f) * (float)(e.levels - 1);
     const LutVal ab = lut_sample(A.lut, A.lut_n, rho, mu);
@@ -403,7 +403,7 @@ __device__ __forceinline__ float3 trace_pixel(const FrameArgs& A, int x, int y, 
   const int max_steps = brute ? INT_MAX : A.max_steps;
 
   const float3 d = pix_dir_world(cam, x, y);
-  const float3 v = d * (-1.0f / sqrtf(dot3(d, d)));
+  const float3 v = view_vector(d);
   const float3 n = ld3(A.normal + 3 * p);
   const float nv = dot3(n, v);
   const float rho = __ldg(A.rough + p), m = __ldg(A.metal + p);
@@ -577,7 +577,7 @@ __device__ __forceinline__ void bwd_mc_pixel(const FrameArgs& A, long long p) {
   if (!is_background(z)) {
     const DevCam& cam = A.vs.cam[view];
     const float3 d = pix_dir_world(cam, x, y);
-    const float3 v = d * (-1.0f / sqrtf(dot3(d, d)));
+    const float3 v = view_vector(d);
     const float3 n = ld3(A.normal + 3 * p);
     const float nv = dot3(n, v);
     const float rho = __ldg(A.rough + p), m = __ldg(A.metal + p);
@@ -698,11 +698,11 @@ __device__ __forceinline__ void bwd_direct_pixel(const FrameArgs& A, long long p
     bilin_adj(A.mips, env_taps(A.e, 0, dir_angles(d)), gcd, 1.0f, A.g_mips, gx, gy);
     return;
   }
-  const float3 v = d * (-1.0f / sqrtf(dot3(d, d)));
+  const float3 v = view_vector(d);
   const float3 n = ld3(A.normal + 3 * p);
   const float nv = dot3(n, v);
   const float mu = fminf(fmaxf(nv, 1e-4f), 1.0f);
-  const float3 r = n * (2.0f * nv) - v;
+  const float3 r = reflect_about(n, nv, v);
   const float rho = __ldg(A.rough + p), m = __ldg(A.metal + p);
   const float lmax = (float)(A.e.levels - 1);
   const float lam = log2f(rho + 1.0f) * lmax;

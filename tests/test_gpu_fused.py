@@ -80,7 +80,7 @@ def test_config4_eight_views_fused_against_per_stage_and_oracle():
     pl = np.sort(rng.choice(V * H * W, size=6000, replace=False))
     r = O.forward(wl, lut=O.build_lut(), pix_list=pl)
     sub = {"hit_idx": got["hit_idx"].reshape(V * H * W, -1)[pl], "final": got["final"].reshape(-1, 3)[pl]}
-    assert_forward_parity(sub, r, "config4 sample")
+    assert_forward_parity(sub, r, "config4 sample", wl=wl, pix=pl)
     assert (sub["hit_idx"] >= 0).mean() > 0.02
 
 
