@@ -32,9 +32,16 @@ if ROOT not in sys.path:
 METRIC = "indirect rays/s & fwd+bwd ms at 1600x900x16spp; serving p50/p99 ms vs plain"
 UNIT = "rays/s"
 L2_FLUSH_BYTES = 512 << 20  # > 126 MB L2: flushed between timed steps, outside the event-timed region
-OPS_PER_STEP = 40           # FP32/INT ops of one march iteration (algorithmic count)
-OPS_PER_SAMPLE = 150        # ops of one traced sample outside the march (RNG, GGX, setup, gather)
-SM_COUNT, FP32_LANES_PER_SM = 152, 128
+# The march is bound by the integer/logic ALU pipe (integer add/logic/shift, compares, min/max,
+# selects): 16 lanes per SM sub-partition per clock, 64 per SM.  Its work is counted in ALU-pipe
+# operations of the source: 29 per march iteration (15 in the cell test every iteration, 21 more
+# on the 64 % of iterations that leave a cell, 1 on the rest that refine) and 100 per traced
+# sample outside the march (Philox's 40, the sampler's and the ray set-up's compares and selects,
+# the lookup's octant selection and texel indexing).
+ALU_OPS_PER_ITER = 29
+ALU_OPS_PER_SAMPLE = 100
+SM_COUNT, ALU_LANES_PER_SM = 152, 64
+SERVE_SUSTAINED_RATE, SERVE_SUSTAINED_REQUESTS = 250.0, 5000
 
 
 def parse():
@@ -81,6 +88,16 @@ def rank_seed(seed: int, rank: int) -> int:
 def workload():
     import ssgi_inputs as si
     return si.config3()
+
+
+def alu_peak_gops(sm_mhz: float) -> float:
+    """ALU-pipe lane operations per second of the GPU (Gop/s)."""
+    return SM_COUNT * ALU_LANES_PER_SM * sm_mhz * 1e6 / 1e9
+
+
+def alu_achieved_gops(iterations: int, samples: int, trace_ms: float) -> float:
+    """Algorithmic ALU-pipe operations of one trace launch per second (Gop/s)."""
+    return (ALU_OPS_PER_ITER * iterations + ALU_OPS_PER_SAMPLE * samples) / (trace_ms / 1e3) / 1e9
 
 
 def config_dict(wl, extra=None):
@@ -146,6 +163,39 @@ class ClockSampler:
         loaded = [s for s in sm if s > 0.5 * (max(mx) if mx else 1)] or sm
         return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+class BusySampler:
+    """nvidia-smi's utilization.gpu (share of each sample period in which a kernel was running)
+    sampled every 100 ms while a phase runs; mean over the phase."""
+
+    def __init__(self, device_index: int):
+        self.idx, self.proc = device_index, None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=utilization.gpu",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        with open(self.path) as f:
+            vals = [float(x) for x in (ln.strip() for ln in f) if x.replace(".", "").isdigit()]
+        os.unlink(self.path)
+        return statistics.mean(vals) / 100.0 if vals else None
 
 
 # ----------------------------------------------------------------------------------------------
@@ -219,6 +269,42 @@ def probe_bandwidth():
     out["method"] = ("ssgi_read_bandwidth_probe: 16-byte ld.global.cg from 8 blocks x 256 threads per SM; "
                      "l2 = a 32 MiB buffer read 64 times per launch, hbm = a 4 GiB buffer read once; best of 5")
     return out
+
+
+def run_config1(flush):
+    """Forward only (env mips, Hi-Z, direct shading, trace) of the 256x256, 4 spp, 32-step
+    single view with a 64x128 map: 12 timed frames after 3 warm-up ones, L2 flushed before each."""
+    import torch
+    import ssgi_inputs as si
+    import paper_2504_01358_gb300 as S
+    wl = si.config1()
+    V, H, W = wl.depth.shape
+    p = S.params_of(wl.params)
+    pipe = S.FramePipeline((V, H, W), wl.env.shape[:2], p, wl.cams)
+    pipe.load(wl)
+    stream = torch.cuda.current_stream()
+    ts, tr = [], []
+    for k in range(15):
+        flush.fill_(float(k))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        pipe.env_mips()
+        pipe.hiz_build()
+        pipe.shade()
+        ev[1].record(stream)
+        pipe.trace()
+        ev[2].record(stream)
+        ev[2].synchronize()
+        if k >= 3:
+            ts.append(ev[0].elapsed_time(ev[2]))
+            tr.append(ev[1].elapsed_time(ev[2]))
+    ms, trace_ms = statistics.mean(ts), statistics.mean(tr)
+    rays = V * H * W * p.spp
+    return {"workload": f"{W}x{H} {p.spp}spp {p.max_steps} steps forward only, ground + 3 boxes, env "
+                        f"{wl.env.shape[0]}x{wl.env.shape[1]} log-normal",
+            "forward_ms": ms, "rays_per_s": rays / (ms / 1e3), "trace_ms": trace_ms,
+            "trace_rays_per_s": rays / (trace_ms / 1e3), "launches_per_frame": pipe.kernels_per_step() - 4,
+            "frames": len(ts), "l2": "flushed before each frame"}
 
 
 def run_fused(steps: int, warmup: int):
@@ -409,6 +495,8 @@ def run_serving(n_requests: int, rate: float, slots: int, budget_gb: float):
                            albedo=h["albedo"], rough=h["rough"], metal=h["metal"], cams=rq["scene"].cams)
         srv.wait(t, 60000)
     tickets = []
+    busy = BusySampler(torch.cuda.current_device())
+    busy.start()
     t0 = time.perf_counter()
     for i, rq in enumerate(reqs):
         while time.perf_counter() - t0 < rq["arrival"]:
@@ -428,6 +516,7 @@ def run_serving(n_requests: int, rate: float, slots: int, budget_gb: float):
             raise RuntimeError(f"request failed: {N.STATUS.get(rc, rc)}")
         lat.append(t_sub - rq["arrival"] + ms / 1e3)
     served_span = max(rq["arrival"] + l for rq, l in zip(reqs, lat)) - reqs[0]["arrival"]
+    served_busy = busy.stop()
     st = srv.stats()
     srv.close()
 
@@ -468,6 +557,7 @@ def run_serving(n_requests: int, rate: float, slots: int, budget_gb: float):
         rq = next(q for q in reqs if q["res"] == r)
         plain_one(rq, outs[r][0])
     plat = []
+    busy.start()
     t0 = time.perf_counter()
     for i, rq in enumerate(reqs):
         while time.perf_counter() - t0 < rq["arrival"]:
@@ -475,6 +565,7 @@ def run_serving(n_requests: int, rate: float, slots: int, budget_gb: float):
         plain_one(rq, outs[rq["res"]][i % ring])
         plat.append(time.perf_counter() - t0 - rq["arrival"])
     plain_span = max(rq["arrival"] + l for rq, l in zip(reqs, plat)) - reqs[0]["arrival"]
+    plain_busy = busy.stop()
 
     def pct(a, q):
         import numpy as np
@@ -484,9 +575,10 @@ def run_serving(n_requests: int, rate: float, slots: int, budget_gb: float):
             "offered_rays_per_s": rays / reqs[-1]["arrival"],
             "served": {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "mean_ms": 1e3 * sum(lat) / len(lat),
                        "throughput_req_per_s": n_requests / served_span, "rays_per_s": rays / served_span,
-                       "arena_peak_gb": st["arena_bytes_peak"] / 2 ** 30},
+                       "arena_peak_gb": st["arena_bytes_peak"] / 2 ** 30, "gpu_busy_share": served_busy},
             "plain": {"p50_ms": pct(plat, 50), "p99_ms": pct(plat, 99), "mean_ms": 1e3 * sum(plat) / len(plat),
-                      "throughput_req_per_s": n_requests / plain_span, "rays_per_s": rays / plain_span},
+                      "throughput_req_per_s": n_requests / plain_span, "rays_per_s": rays / plain_span,
+                      "gpu_busy_share": plain_busy},
             "p99_plain_over_served": pct(plat, 99) / max(pct(lat, 99), 1e-9),
             "workload": "Poisson arrivals, resolution uniform over 640x360/1280x720/1600x900/1920x1080, spp uniform "
                         "over 4/8/16/32, scenes from the config-2 generator (pool of 4 per resolution), 128x256 "
@@ -589,9 +681,31 @@ def run_ours(args):
         b.synchronize()
         ts.append(a.elapsed_time(b))
     dn_ms = statistics.mean(ts[3:])
+
+    def timed_ms(fn, n=13, skip=3):
+        out = []
+        for k in range(n):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            out.append(a.elapsed_time(b))
+        return statistics.mean(out[skip:])
+
+    # the normals fused into the pyramid's pass over depth, against the two passes
+    sep_ms = timed_ms(lambda: (S.ssgi_build_hiz(pipe.g.depth, p.hiz_levels, out=pipe.hiz),
+                               S.ssgi_depth_normals(pipe.g.depth, pipe.cam, out=nrm)))
+    fus_ms = timed_ms(lambda: S.ssgi_build_hiz_normals(pipe.g.depth, pipe.cam, p.hiz_levels, hiz=pipe.hiz,
+                                                        normals=nrm))
     depth_normals = {"ms": dn_ms, "algorithmic_bytes": 16 * V * H * W,
                      "achieved_gbs": 16 * V * H * W / (dn_ms / 1e3) / 1e9, "launches": 1,
-                     "note": "ssgi_depth_normals at the step's frame, L2 flushed before each of 10 timed calls"}
+                     "note": "ssgi_depth_normals at the step's frame, L2 flushed before each of 10 timed calls",
+                     "with_pyramid": {"separate_ms": sep_ms, "separate_launches": 3, "fused_ms": fus_ms,
+                                      "fused_launches": 2,
+                                      "note": "ssgi_build_hiz + ssgi_depth_normals vs ssgi_build_hiz_normals "
+                                              "(one read of depth), same outputs bit for bit"}}
     del nrm
 
     # object insertion into the same frame (Sec. 4): a floating box rendered on its own and merged
@@ -637,10 +751,22 @@ def run_ours(args):
     gfs = torch.empty_like(pipe.final)
     tm_ms = epilogue_ms(lambda: S.ssgi_tonemap_srgb(pipe.final, out=srgb))
     ls_ms = epilogue_ms(lambda: S.ssgi_l2_loss_srgb(pipe.final, pipe.target, g_final=gfs, loss=pipe.loss))
+    # the transform as the trace's epilogue (SSGI_SRGB_FINAL) against trace + separate pass
+    from paper_2504_01358_gb300._native import SRGB_FINAL as N_SRGB_FINAL
+    p_srgb = S.TraceParams(p.spp, p.max_steps, p.hiz_levels, p.thickness, p.max_distance, p.seed,
+                           p.flags | N_SRGB_FINAL)
+    two_ms = epilogue_ms(lambda: (pipe.trace(), S.ssgi_tonemap_srgb(pipe.final, out=srgb)))
+    one_ms = epilogue_ms(lambda: S.ssgi_trace_indirect(pipe.g, pipe.cam, pipe.hiz, pipe.c1, pipe.c_d, pipe.em, p_srgb,
+                                                       final=srgb, hit_idx=pipe.hit_idx))
     output_transform = {"tonemap_ms": tm_ms, "tonemap_gbs": 24 * V * H * W / (tm_ms / 1e3) / 1e9,
                         "srgb_loss_ms": ls_ms, "srgb_loss_gbs": 36 * V * H * W / (ls_ms / 1e3) / 1e9,
-                        "note": "ssgi_tonemap_srgb and ssgi_l2_loss_srgb at the step's frame, L2 flushed"}
+                        "trace_then_tonemap_ms": two_ms, "trace_with_srgb_epilogue_ms": one_ms,
+                        "note": "ssgi_tonemap_srgb and ssgi_l2_loss_srgb at the step's frame, L2 flushed; the "
+                                "trace with SSGI_SRGB_FINAL writes the display image itself (same bits)"}
     del srgb, gfs
+
+    # the small single-view workload (256x256, 4 spp, 32 steps, 64x128 map): forward only
+    cfg1 = run_config1(flush)
 
     # march iterations of one trace launch (counted by the kernel itself, untimed)
     counter = torch.zeros(1, device="cuda", dtype=torch.int64)
@@ -734,18 +860,19 @@ def run_ours(args):
 
     peaks, peak_src = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / 1e9  # Gop/s
-    alg_ops = OPS_PER_STEP * iters + OPS_PER_SAMPLE * valid
-    achieved = alg_ops / (trace_ms / 1e3) / 1e9
+    alu_peak = alu_peak_gops(sm_max)
+    achieved = alu_achieved_gops(iters, valid, trace_ms)
     prof = profile_summary()
     traffic = profiled(prof, "dram_bytes_per_launch")
     bw = probe_bandwidth()
     l2_bytes = profiled(prof, "lts_bytes_per_launch")
     roofline = {"kernel": "k_trace (ssgi_trace_indirect)", "bound": "alu", "achieved": achieved, "peak": alu_peak,
                 "unit": "Gop/s", "frac": achieved / alu_peak, "traffic": traffic,
-                "peak_source": f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz "
-                               f"({peak_src} max SM clock)",
-                "work": f"{OPS_PER_STEP} ops x {iters} march iterations + {OPS_PER_SAMPLE} ops x {valid} traced samples",
+                "peak_source": f"derived: {SM_COUNT} SMs x {ALU_LANES_PER_SM} integer/logic ALU-pipe lanes x "
+                               f"{sm_max:.0f} MHz ({peak_src} max SM clock)",
+                "work": {"alu_ops_per_march_iteration": ALU_OPS_PER_ITER, "alu_ops_per_traced_sample": ALU_OPS_PER_SAMPLE,
+                         "march_iterations": iters, "traced_samples": valid,
+                         "achieved = (ops_per_iteration x iterations + ops_per_sample x samples) / trace_ms": True},
                 "trace_ms": trace_ms, "march_iterations": iters, "traced_samples": valid,
                 "hbm_algorithmic_gbs": (V * H * W * (36 + 12 + 12) + 4 * V * H * W * p.spp) / (trace_ms / 1e3) / 1e9,
                 "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
@@ -768,11 +895,13 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl)
-    serving = None
+    serving = serving_sustained = None
     if rank == 0 and not args.no_serving:
         pipe = None
         torch.cuda.empty_cache()
         serving = run_serving(args.serve_requests, args.serve_rate, args.serve_slots, 100.0)
+        # a load the plain path also sustains, so that its latency is not a growing queue
+        serving_sustained = run_serving(SERVE_SUSTAINED_REQUESTS, SERVE_SUSTAINED_RATE, args.serve_slots, 100.0)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -783,10 +912,11 @@ def run_ours(args):
                 "stage_ms": stage_ms, "wall_s": t_wall,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "bandwidth_probe": bw, "adjoint_modes": adjoints,
+                "config1_forward": cfg1,
                 "depth_normals": depth_normals, "object_insertion": composite,
                 "output_transform": output_transform,
                 "fused_step": fused,
-                "serving": serving}
+                "serving": serving, "serving_sustained": serving_sustained}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -79,6 +79,8 @@ typedef enum {
 #define SSGI_BRUTE_FORCE 2u      /* ignore the pyramid: walk every pixel, no step budget (reference mode) */
 #define SSGI_PATHWISE 4u         /* backward only: pathwise gradients through the sampled directions */
 #define SSGI_SRGB_LOSS 8u        /* fused step only: the L2 loss compares the sRGB image (ssgi_l2_loss_srgb) */
+#define SSGI_SRGB_FINAL 16u      /* trace only: final_out receives the display image, ssgi_tonemap_srgb of the
+                                    composite (Sec. 3.3), written by the trace itself; not for ssgi_step_fused */
 
 typedef struct { int32_t views, height, width; } ssgi_dims;
 
@@ -111,7 +113,7 @@ typedef struct {
   float thickness;    /* a hit needs the ray to pass behind the depth buffer by at most this (world units) */
   float max_distance; /* ray length in world units (> 0) */
   uint64_t seed;      /* RNG key */
-  uint32_t flags;     /* SSGI_DIFFUSE_INDIRECT | SSGI_BRUTE_FORCE | SSGI_PATHWISE | SSGI_SRGB_LOSS */
+  uint32_t flags;     /* SSGI_DIFFUSE_INDIRECT | SSGI_BRUTE_FORCE | SSGI_PATHWISE | SSGI_SRGB_LOSS | SSGI_SRGB_FINAL */
 } ssgi_trace_params;
 
 /* ---------------------------------------------------------------------------------------- */
@@ -174,7 +176,10 @@ ssgi_status ssgi_shade_direct(const ssgi_gbuffer *g, const ssgi_camera *cams, co
  * SSGI_BRUTE_FORCE).  c1, c_d: ssgi_shade_direct outputs.  Outputs: final [V,H,W,3];
  * c_s_mc, c_id [V,H,W,3] and hit_idx [V,H,W,spp] are optional (NULL).  step_count (one
  * device uint64, optional) has the total number of march iterations of the call added to
- * it atomically (the caller zeroes it); this is the traversal work of the launch. */
+ * it atomically (the caller zeroes it); this is the traversal work of the launch.  With
+ * SSGI_SRGB_FINAL final holds the display image (the composite's output transform, clamp to
+ * [0, 1] and the sRGB transfer function, equal to ssgi_tonemap_srgb of the linear final),
+ * applied in the trace's own epilogue: no separate pass over the image. */
 ssgi_status ssgi_trace_indirect(const ssgi_gbuffer *g, const ssgi_camera *cams, const float *hiz, const float *c1,
                                 const float *c_d, const ssgi_envmap *env, const ssgi_trace_params *p,
                                 float *c_s_mc, float *c_id, float *final_out, int32_t *hit_idx,
@@ -398,6 +403,13 @@ ssgi_status ssgi_composite_gbuffer(const ssgi_gbuffer *scene, const ssgi_gbuffer
 /* ---------------------------------------------------------------------------------------- */
 ssgi_status ssgi_depth_normals(const float *depth, ssgi_dims d, const ssgi_camera *cams, float *normal_out,
                                ssgi_stream_t stream);
+/* Depth normals and the Hi-Z pyramid in one pass over depth (the two above fused: the depth
+ * normals of Sec. 3.1 computed while the pyramid's tiles are read, no second read of depth).
+ * normal_out [V,H,W,3] equals ssgi_depth_normals' and hiz_out equals ssgi_build_hiz's for the
+ * same arguments, bit for bit.  levels as for ssgi_build_hiz (hiz_out may be NULL with
+ * levels == 1: normals only). */
+ssgi_status ssgi_build_hiz_normals(const float *depth, ssgi_dims d, const ssgi_camera *cams, int32_t levels,
+                                   float *hiz_out, float *normal_out, ssgi_stream_t stream);
 
 /* ---------------------------------------------------------------------------------------- */
 /* Measurement: a read-bandwidth probe.  Streams `bytes` of device memory at `buf` `reps` times */

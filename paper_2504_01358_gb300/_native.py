@@ -19,6 +19,7 @@ DIFFUSE_INDIRECT = 1
 BRUTE_FORCE = 2
 PATHWISE = 4
 SRGB_LOSS = 8
+SRGB_FINAL = 16
 
 STATUS = {
     0: "SSGI_OK", 1: "SSGI_ERR_INVALID_ARG", 2: "SSGI_ERR_UNSUPPORTED", 3: "SSGI_ERR_CUDA", 4: "SSGI_ERR_OOM",
@@ -106,6 +107,7 @@ _SIGS = {
     "ssgi_step_fused_phase_ns": (C.c_int, [VP, C.POINTER(C.c_uint64)]),
     "ssgi_read_bandwidth_probe": (C.c_int, [VP, SZ, I32, VP, VP]),
     "ssgi_depth_normals": (C.c_int, [VP, Dims, C.POINTER(Camera), VP, VP]),
+    "ssgi_build_hiz_normals": (C.c_int, [VP, Dims, C.POINTER(Camera), I32, VP, VP, VP]),
     "ssgi_tonemap_srgb": (C.c_int, [VP, VP, I64, VP]),
     "ssgi_l2_loss_srgb": (C.c_int, [VP, VP, I64, VP, VP, VP]),
     "ssgi_env_keyframe_lerp": (C.c_int, [VP, VP, C.c_float, I32, I32, VP, VP]),

@@ -86,7 +86,7 @@ ssgi_status trace_params_ok(const ssgi_trace_params* p) {
   if (p->spp < 1 || p->spp > 1024 || p->max_steps < 0) return SSGI_ERR_INVALID_ARG;
   if (p->hiz_levels < 1 || p->hiz_levels > SSGI_MAX_HIZ_LEVELS) return SSGI_ERR_INVALID_ARG;
   if (!(p->thickness >= 0.0f) || !(p->max_distance > 0.0f)) return SSGI_ERR_INVALID_ARG;
-  if (p->flags & ~(uint32_t)(SSGI_DIFFUSE_INDIRECT | SSGI_BRUTE_FORCE | SSGI_PATHWISE | SSGI_SRGB_LOSS))
+  if (p->flags & ~(uint32_t)(SSGI_DIFFUSE_INDIRECT | SSGI_BRUTE_FORCE | SSGI_PATHWISE | SSGI_SRGB_LOSS | SSGI_SRGB_FINAL))
     return SSGI_ERR_INVALID_ARG;
   return SSGI_OK;
 }

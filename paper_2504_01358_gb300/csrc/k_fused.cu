@@ -291,7 +291,7 @@ ssgi_status ssgi_step_fused(const ssgi_gbuffer* g, const ssgi_camera* cams, cons
   if (gbuffer_ok(g) != SSGI_OK || trace_params_ok(p) != SSGI_OK || !env || !lut || lut_n < 2 || !target ||
       !final_out || !hit_idx || !loss || !g_albedo || !g_rough || !g_metal || !g_normal || !g_env || !workspace)
     return SSGI_ERR_INVALID_ARG;
-  if (p->flags & SSGI_BRUTE_FORCE) return SSGI_ERR_INVALID_ARG;
+  if (p->flags & (SSGI_BRUTE_FORCE | SSGI_SRGB_FINAL)) return SSGI_ERR_INVALID_ARG;
   if (((uintptr_t)workspace & 255) != 0) return SSGI_ERR_INVALID_ARG;
   const size_t need = ssgi_step_fused_workspace_bytes(g->d, env_h, env_w, p->hiz_levels);
   if (need == 0 || ws_bytes < need) return SSGI_ERR_INVALID_ARG;

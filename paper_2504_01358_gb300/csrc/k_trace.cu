@@ -27,7 +27,7 @@ constexpr int kTileH = 16;  // a 128-thread block covers 8 x 16 pixels
 // rays start close together and touch the same pyramid cells.  Seven blocks per SM leave 72
 // registers a thread, enough for the march and the pixel's shading inputs without spills
 // (measured faster than eight blocks at 64 registers and six at 80).
-template <bool kCid>
+template <bool kCid, bool kSrgb>
 __global__ void __launch_bounds__(kTileW * kTileH, 7) k_trace(FrameArgs A) {
   __shared__ LevelTable s_lv;
   fill_levels(A, blockIdx.z, s_lv);
@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(kTileW * kTileH, 7) k_trace(FrameArgs A) {
   const int x = blockIdx.x * kTileW + (threadIdx.x % kTileW);
   const int y = blockIdx.y * kTileH + (threadIdx.x / kTileW);
   if (x >= A.vs.W || y >= A.vs.H) return;
-  trace_pixel<kCid>(A, x, y, blockIdx.z, s_lv);
+  trace_pixel<kCid, kSrgb>(A, x, y, blockIdx.z, s_lv);
 }
 
 }  // namespace ssgi
@@ -75,9 +75,8 @@ extern "C" ssgi_status ssgi_trace_indirect(const ssgi_gbuffer* g, const ssgi_cam
   A.seed = p->seed;
   A.flags = p->flags;
   dim3 grid(ceil_div(g->d.width, kTileW), ceil_div(g->d.height, kTileH), g->d.views);
-  if (p->flags & SSGI_DIFFUSE_INDIRECT)
-    k_trace<true><<<grid, kTileW * kTileH, 0, (cudaStream_t)stream>>>(A);
-  else
-    k_trace<false><<<grid, kTileW * kTileH, 0, (cudaStream_t)stream>>>(A);
+  const bool cid = (p->flags & SSGI_DIFFUSE_INDIRECT) != 0, srgb = (p->flags & SSGI_SRGB_FINAL) != 0;
+  auto kern = cid ? (srgb ? k_trace<true, true> : k_trace<true, false>) : (srgb ? k_trace<false, true> : k_trace<false, false>);
+  kern<<<grid, kTileW * kTileH, 0, (cudaStream_t)stream>>>(A);
   return launch_status();
 }

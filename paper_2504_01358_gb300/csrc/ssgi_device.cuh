@@ -26,8 +26,11 @@ __device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x 
 __device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
 __device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(a.x * s, a.y * s, a.z * s); }
 __device__ __forceinline__ float3 mul3(float3 a, float3 b) { return f3(a.x * b.x, a.y * b.y, a.z * b.z); }
-// x y z order, one rounding per step (never re-fused by the compiler)
-__device__ __forceinline__ float dot3(float3 a, float3 b) {
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+// The same in x y z order with one rounding per step, never re-fused by the compiler: for the
+// dot products that shape a sampled direction or a lookup coordinate (n.v, v.h, |d|^2), whose
+// bits a host model reproduces.  (Everywhere else the compiler's own fusion measured faster.)
+__device__ __forceinline__ float dot3_rn(float3 a, float3 b) {
   return __fmaf_rn(a.z, b.z, __fmaf_rn(a.y, b.y, __fmul_rn(a.x, b.x)));
 }
 __device__ __forceinline__ float3 ld3(const float* __restrict__ p) { return f3(__ldg(p), __ldg(p + 1), __ldg(p + 2)); }
@@ -55,7 +58,7 @@ __device__ __forceinline__ float3 pix_dir_world(const DevCam& c, int x, int y) {
 }
 // Unit vector from the surface point of a pixel to the camera: -d / |d| for the pixel's ray d.
 __device__ __forceinline__ float3 view_vector(float3 d) {
-  const float s = __fdiv_rn(-1.0f, __fsqrt_rn(dot3(d, d)));
+  const float s = __fdiv_rn(-1.0f, __fsqrt_rn(dot3_rn(d, d)));
   return f3(__fmul_rn(d.x, s), __fmul_rn(d.y, s), __fmul_rn(d.z, s));
 }
 // Mirror direction r = 2 (v.n) n - v.
@@ -227,7 +230,7 @@ struct Sample {
 __device__ __forceinline__ Sample make_sample(float3 n, float3 v, float nv, float rho, float2 xi) {
   Sample s;
   s.h = ggx_sample_h(n, rho, xi.x, xi.y, &s.nh, &s.ds);
-  s.vh = dot3(v, s.h);
+  s.vh = dot3_rn(v, s.h);
   s.w = reflect_about(s.h, s.vh, v);
   s.nw = fmaf(2.0f * s.vh, s.nh, -nv);
   s.valid = (nv > 0.0f) && (s.nw > 0.0f) && (s.vh > 0.0f) && (s.nh > 0.0f);

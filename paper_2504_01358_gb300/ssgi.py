@@ -358,6 +358,20 @@ def ssgi_depth_normals(depth: torch.Tensor, cams, out: Optional[torch.Tensor] = 
     return out
 
 
+def ssgi_build_hiz_normals(depth: torch.Tensor, cams, levels: int, hiz: Optional[torch.Tensor] = None,
+                           normals: Optional[torch.Tensor] = None, stream=None):
+    """(pyramid, normals) from one pass over depth: ssgi_build_hiz and ssgi_depth_normals fused."""
+    V, H, W = depth.shape
+    if hiz is None and levels > 1:
+        hiz = torch.empty(max(ssgi_hiz_floats((V, H, W), levels), 1), device=depth.device, dtype=torch.float32)
+    if normals is None:
+        normals = torch.empty((V, H, W, 3), device=depth.device, dtype=torch.float32)
+    cam = cams if isinstance(cams, C.Array) else cameras(cams)
+    N.call("ssgi_build_hiz_normals", _dev(depth, "depth"), N.Dims(V, H, W), cam, levels, _dev(hiz, "hiz_out"),
+           _dev(normals, "normal_out"), _stream(stream))
+    return hiz, normals
+
+
 def ssgi_read_bandwidth_probe(buf: torch.Tensor, reps: int, sink: Optional[torch.Tensor] = None,
                               stream=None) -> None:
     """Streams the bytes of `buf` (a contiguous CUDA tensor) `reps` times through L2."""

@@ -43,7 +43,10 @@ def test_profiled_tolerates_missing_and_malformed_values():
 
 
 def test_whole_job_rate_and_alu_peak_arithmetic():
-    # 152 SMs x 128 FP32 lanes x 2070 MHz = 40.27 Tops/s, the roofline's derived ALU peak
-    assert bench.SM_COUNT * bench.FP32_LANES_PER_SM * 2070.0 * 1e6 / 1e9 == pytest.approx(40273.92)
+    # 152 SMs x 64 ALU-pipe lanes x 2070 MHz = 20.14 T lane-ops/s, the roofline's derived ALU peak
+    assert bench.alu_peak_gops(2070.0) == pytest.approx(20136.96)
+    # the achieved figure reproduces from the line's fields: 29 ops x iterations + 100 x samples
+    assert bench.alu_achieved_gops(320_000_000, 12_700_000, 2.5) == pytest.approx(
+        (29 * 320e6 + 100 * 12.7e6) / 2.5e-3 / 1e9)
     # one rank, 23.04 M rays in 3.2 ms
     assert bench.whole_job_rate(23040000.0, 1, 3.2) == pytest.approx(7.2e9)

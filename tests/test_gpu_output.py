@@ -61,3 +61,28 @@ def test_keyframe_blend_and_adjoint(S):
     np.testing.assert_allclose(gb.cpu().numpy(), 0.25 * g, rtol=1e-6, atol=1e-6)
     S.ssgi_env_keyframe_lerp_backward(_t(g), 0.25, ga, gb, accumulate=False)
     np.testing.assert_allclose(ga.cpu().numpy(), 0.75 * g, rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("flags", [0, 1])
+def test_trace_srgb_epilogue_equals_the_separate_transform(S, flags):
+    """SSGI_SRGB_FINAL: the trace writes the display image itself (the output transform as its
+    epilogue), bit for bit the separate ssgi_tonemap_srgb of its linear final, on foreground and
+    background pixels; the linear parts and the hits are unchanged, and the oracle's transform of
+    the oracle's final agrees to the transfer function's bound."""
+    import ssgi_inputs as si
+    from parity import gpu_forward
+    wl = si.small_case()
+    base = gpu_forward(wl, flags=flags)
+    enc = gpu_forward(wl, flags=flags | S._native.SRGB_FINAL)
+    assert np.array_equal(enc["hit_idx"], base["hit_idx"])
+    assert np.array_equal(enc["cs_mc"], base["cs_mc"])
+    sep = S.ssgi_tonemap_srgb(_t(base["final"])).cpu().numpy()
+    assert np.array_equal(enc["final"], sep)
+    r = O.forward(wl, lut=O.build_lut(), flags=flags)
+    assert np.abs(enc["final"] - O.tonemap_srgb(r["final"])).max() <= 1e-4
+    # not a flag of the fused step (its loss reads the linear image)
+    g, env, cams, tgt = S.to_device_workload(wl)
+    p = S.params_of(wl.params)
+    p.flags |= S._native.SRGB_FINAL
+    with pytest.raises(S._native.SSGIError):
+        S.ssgi_step_fused(g, cams, env, S.ssgi_build_brdf_lut(), tgt, p)
