@@ -291,16 +291,27 @@ __device__ __forceinline__ void split_coord(float base, float ang, int n, float 
   i0 = (int)f0;
 }
 
+// kMask: wrap the column with a mask (the map's widths are powers of two, and a two's-complement
+// mask wraps negative columns too) instead of a remainder and two tests: the same taps, measured
+// 9 % faster in direct shading and 2.5 % in the adjoint, but 0.6 % slower in the trace, whose
+// miss lookup keeps the remainder.
+template <bool kMask = true>
 __device__ __forceinline__ Taps env_taps(const EnvInfo& e, int l, const DirAngles& a) {
   Taps t;
   const int h = e.h[l], w = e.w[l];
   int x0, y0;
   split_coord(a.bx, a.ax, w, __fmul_rn((float)w, kInv2Pi), x0, t.tx);
   split_coord(a.by, a.ay, h, __fmul_rn((float)h, kInvPi), y0, t.ty);
-  int c0 = x0 % w;
-  if (c0 < 0) c0 += w;
-  int c1 = c0 + 1;
-  if (c1 >= w) c1 -= w;
+  int c0, c1;
+  if (kMask) {
+    c0 = x0 & (w - 1);
+    c1 = (x0 + 1) & (w - 1);
+  } else {
+    c0 = x0 % w;
+    if (c0 < 0) c0 += w;
+    c1 = c0 + 1;
+    if (c1 >= w) c1 -= w;
+  }
   const int r0 = min(max(y0, 0), h - 1), r1 = min(max(y0 + 1, 0), h - 1);
   const int base = e.off[l];
   t.idx[0] = base + (r0 * w + c0) * 3;
@@ -334,6 +345,10 @@ __device__ __forceinline__ float3 env_lookup(const float* __restrict__ mips, con
 
 __device__ __forceinline__ float3 env_lookup0(const float* __restrict__ mips, const EnvInfo& e, float3 d) {
   return bilinear(mips, env_taps(e, 0, dir_angles(d)));
+}
+// The trace's miss lookup (see env_taps).
+__device__ __forceinline__ float3 env_lookup0_trace(const float* __restrict__ mips, const EnvInfo& e, float3 d) {
+  return bilinear(mips, env_taps<false>(e, 0, dir_angles(d)));
 }
 
 // ------------------------------------------------------------------------------------------
