@@ -518,21 +518,24 @@ __device__ __forceinline__ void atomic_add4(float4* p, float3 v) {
   if (lane == __ffs(grp) - 1) atomicAdd(p, make_float4(v.x, v.y, v.z, 0.0f));
 }
 
-// d ln G1(z; rho) / dz, / drho
+// d ln G1(z; rho) / dz, / drho.  The adjoint's own quotients use the approximate division
+// (__fdividef, 2 ulp): the gradients are compared at 1e-3, and it measured 3.4 % faster.
+// Anything that shapes a direction, a hit or the forward's radiance keeps IEEE division.
 __device__ __forceinline__ void dlnG1(float z, float rho, float& dz, float& dr) {
   const float a2 = rho * rho;
   const float s = sqrtf(a2 + (1.0f - a2) * z * z);
-  dz = 1.0f / z - (1.0f + (1.0f - a2) * z / s) / (z + s);
-  dr = -(rho * (1.0f - z * z) / s) / (z + s);
+  const float izs = __fdividef(1.0f, z + s), is = __fdividef(1.0f, s);
+  dz = __fdividef(1.0f, z) - (1.0f + (1.0f - a2) * z * is) * izs;
+  dr = -(rho * (1.0f - z * z) * is) * izs;
 }
 
 // d ln D(c; rho) / dc, / drho with c = n.h, at a half vector drawn by ggx_sample_h with
 // denominator ds (1 + c^2 (rho^2 - 1) = rho^2 / ds there, see ggx_D_sampled):
 //   dc = -4 c (rho^2 - 1) / (1 + c^2 (rho^2 - 1)),  dr = 2 / rho - 4 rho c^2 / (1 + c^2 (rho^2 - 1)).
 __device__ __forceinline__ void dlnD(float c, float ds, float rho, float& dc, float& dr) {
-  const float q = ds / (rho * rho);  // 1 / (1 + c^2 (rho^2 - 1))
+  const float q = __fdividef(ds, rho * rho);  // 1 / (1 + c^2 (rho^2 - 1))
   dc = 4.0f * c * (1.0f - rho * rho) * q;
-  dr = 2.0f / rho - 4.0f * rho * c * c * q;
+  dr = __fdividef(2.0f, rho) - 4.0f * rho * c * c * q;
 }
 
 // Scatter g (per channel) with weight `scale` through the bilinear taps into gm, and return
@@ -592,8 +595,9 @@ __device__ __forceinline__ float3 env_lookup_adj(const float* __restrict__ mips,
   if (!(q2 > 0.0f)) return f3(0.f, 0.f, 0.f);
   const float q = sqrtf(q2);
   const float r2 = q2 + d.y * d.y;
-  const float dux = -d.z * kInv2Pi / q2, duz = d.x * kInv2Pi / q2;
-  const float dvx = d.y * d.x * kInvPi / (q * r2), dvz = d.y * d.z * kInvPi / (q * r2), dvy = -q * kInvPi / r2;
+  const float iq2 = __fdividef(kInv2Pi, q2), iqr = __fdividef(kInvPi, q * r2);
+  const float dux = -d.z * iq2, duz = d.x * iq2;
+  const float dvx = d.y * d.x * iqr, dvz = d.y * d.z * iqr, dvy = __fdividef(-q * kInvPi, r2);
   return f3(gu * dux + gv * dvx, gv * dvy, gu * duz + gv * dvz);
 }
 
@@ -639,7 +643,7 @@ __device__ __forceinline__ void bwd_mc_pixel(const FrameArgs& A, long long p) {
         tm = env_taps(A.e, 0, dir_angles(sm.w));
         Li = bilinear(A.mips, tm);
       }
-      const float K = ggx_G1(sm.nw, rho) * g1v * sm.vh / (nv * sm.nh);
+      const float K = __fdividef(ggx_G1(sm.nw, rho) * g1v * sm.vh, nv * sm.nh);
       const float fc = pow5(1.0f - sm.vh);
       const float3 F = F0 + (f3(1.f, 1.f, 1.f) - F0) * fc;
       float3 gL = mul3(gC, F) * K;
@@ -761,7 +765,7 @@ __device__ __forceinline__ void bwd_direct_pixel(const FrameArgs& A, long long p
   if (nv > 1e-4f && nv < 1.0f) gnv = gA * ab.dA_dmu + gB * ab.dB_dmu;
   // r = 2 (n.v) n - v
   const float3 gn = gdn + v * (2.0f * dot3(gdr, n)) + gdr * (2.0f * nv) + v * gnv;
-  const float gr = gA * ab.dA_drho + gB * ab.dB_drho + (gl1 + gl2) * lmax / ((rho + 1.0f) * 0.69314718055994531f);
+  const float gr = gA * ab.dA_drho + gB * ab.dB_drho + __fdividef((gl1 + gl2) * lmax, (rho + 1.0f) * 0.69314718055994531f);
   float* pa = A.g_albedo + 3 * p;
   float* pn = A.g_normal + 3 * p;
   st3(pa, ld3(pa) + ga);
