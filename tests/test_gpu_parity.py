@@ -358,3 +358,42 @@ def test_autograd_function_matches_backward_call(S, small, olut):
         assert np.abs(a - b).max() <= 1e-5 * max(np.abs(b).max(), 1e-12), k
     a, b = env_l.grad.cpu().numpy(), gr["env"].cpu().numpy()
     assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max()
+
+
+# --------------------------------------------------------------------------------------------
+# the interface's maximum sizes
+# --------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["32views", "16384wide", "1024spp", "16levels"])
+def test_maximum_sizes_match_oracle(S, olut, case):
+    """The limits include/ssgi.h states, each at its maximum: SSGI_MAX_VIEWS (32) views of one
+    scene; a frame 16384 pixels wide (the width limit; 3 rows, so the pyramid's top levels are
+    ragged 1-row strips); 1024 samples per pixel (the spp limit); 16 pyramid levels (the level
+    limit, above the frame's own height) -- forward against the oracle on every pixel, backward
+    on the 32-view case."""
+    scene = si.make_scene(61, 8, 3.0, 1)
+    if case == "32views":
+        cams = [si.look_at((4.5 * np.sin(a), 1.4 + 0.3 * np.cos(3 * a), 4.5 * np.cos(a)), (0, 0.3, 0))
+                for a in np.linspace(0.0, 2 * np.pi, 32, endpoint=False)]
+        H, W, params = 12, 20, si.TraceParams(spp=4, max_steps=32, seed=61)
+    elif case == "16384wide":
+        cams = [si.look_at((0.0, 1.6, 5.0), (0.0, 0.5, 0.0), fov_y_deg=2.0)]
+        H, W, params = 3, 16384, si.TraceParams(spp=2, max_steps=64, seed=62)
+    elif case == "1024spp":
+        cams = [si.look_at((0.0, 1.6, 5.0), (0.0, 0.5, 0.0))]
+        H, W, params = 6, 7, si.TraceParams(spp=1024, max_steps=32, seed=63)
+    else:
+        cams = [si.look_at((0.0, 1.6, 5.0), (0.0, 0.5, 0.0))]
+        H, W, params = 33, 47, si.TraceParams(spp=4, max_steps=48, hiz_levels=16, seed=64)
+    bufs = [si.raycast_gbuffer(scene, c, H, W) for c in cams]
+    st = lambda k: np.stack([b[k] for b in bufs])  # noqa: E731
+    wl = si.Workload(f"max-{case}", st("depth"), st("normal"), st("albedo"), st("rough"), st("metal"),
+                     np.stack(cams), si.lognormal_env(65, 16, 32), params,
+                     si.uniform_target(66, len(cams), H, W))
+    g = gpu_forward(wl)
+    r = orc_forward(wl, lut=olut)
+    assert_forward_parity(g, r, f"maximum {case}", wl=wl)
+    assert_direct_parity(g, r, wl, f"maximum {case}", keys=("c1",))
+    assert np.isfinite(wl.depth).any()
+    if case == "32views":
+        _assert_backward_parity(*_backward_pair(S, wl, olut, 0), label="maximum 32views",
+                                kinks=direct_kinks(wl))
