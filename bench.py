@@ -308,7 +308,7 @@ def run_config1(flush):
 
 
 def run_fused(steps: int, warmup: int):
-    """The multi-view step (8 views at 1245x825, 32 spp, one 512x1024 env) as one persistent
+    """The multi-view step (8 views at 1245x825, 32 spp, one 512x1024 env) as one
     launch (ssgi_step_fused) and, for comparison, as the per-stage calls."""
     import torch
     import ssgi_inputs as si
@@ -343,7 +343,7 @@ def run_fused(steps: int, warmup: int):
 
     f_ms = timed(fused)
     if S.ssgi_step_fused_check(ws):
-        raise RuntimeError("fused step stopped at a grid barrier")
+        raise RuntimeError("a block of the fused step gave up waiting for the previous phase")
     phases = {k: v / 1e6 for k, v in S.ssgi_step_fused_phase_ns(ws).items()}
     s_ms = timed(pipe.step)
     rays = V * H * W * p.spp

@@ -218,36 +218,38 @@ ssgi_status ssgi_backward(const float *g_final, const ssgi_gbuffer *g, const ssg
                           float *g_normal, float *g_env, void *workspace, size_t ws_bytes, ssgi_stream_t stream);
 
 /* ---------------------------------------------------------------------------------------- */
-/* Fused inverse-rendering step: every stage above for all views of a frame in ONE persistent  */
-/* cooperative launch (env mips, Hi-Z, direct shading, trace with stored hits, L2 loss against */
-/* `target`, backward).  Same per-item code as the separate calls, so final and hit_idx equal  */
-/* theirs bit for bit and the gradients agree up to the order of atomic additions.            */
+/* Fused inverse-rendering step: every stage above for all views of a frame in ONE launch     */
+/* (env mips, Hi-Z, direct shading, trace with stored hits, L2 loss against `target`,         */
+/* backward): one block per work item, phase after phase, each block of a phase waiting       */
+/* (bounded) until the previous phase has finished.  Same per-item code as the separate calls, */
+/* so final and hit_idx equal theirs bit for bit and the gradients agree up to the order of    */
+/* atomic additions.                                                                          */
 /* ---------------------------------------------------------------------------------------- */
 /* workspace bytes of ssgi_step_fused (mips, pyramid, c_d, c1, g_final and the backward scratch) */
 size_t ssgi_step_fused_workspace_bytes(ssgi_dims d, int32_t env_h, int32_t env_w, int32_t hiz_levels);
 /* env: device base level [env_h][env_w][3]; target: device [V,H,W,3]; outputs: final_out
  * [V,H,W,3], hit_idx [V,H,W,spp], loss (one device float), gradients as ssgi_backward.
- * workspace: 256-byte aligned, >= ssgi_step_fused_workspace_bytes.  SSGI_ERR_UNSUPPORTED
- * without cooperative-launch support.  The stages are separated by a grid barrier whose wait is
- * bounded; if a block ever gives up waiting every block stops and ssgi_step_fused_check
- * reports it (the outputs are then incomplete). */
+ * workspace: 256-byte aligned, >= ssgi_step_fused_workspace_bytes.  A block's wait for the
+ * previous phase is bounded; if a block ever gives up waiting every later block stops and
+ * ssgi_step_fused_check reports it (the outputs are then incomplete). */
 ssgi_status ssgi_step_fused(const ssgi_gbuffer *g, const ssgi_camera *cams, const float *env, int32_t env_h,
                             int32_t env_w, const float *lut, int32_t lut_n, const float *target,
                             const ssgi_trace_params *p, float *final_out, int32_t *hit_idx, float *loss,
                             float *g_albedo, float *g_rough, float *g_metal, float *g_normal, float *g_env,
                             void *workspace, size_t ws_bytes, ssgi_stream_t stream);
-/* Synchronous: *failed = 1 if the last fused step on this workspace stopped at a barrier. */
+/* Synchronous: *failed = 1 if a block of the last fused step on this workspace gave up waiting. */
 ssgi_status ssgi_step_fused_check(const void *workspace, int32_t *failed);
-/* How long a block of later ssgi_step_fused launches waits at a grid barrier before it gives
- * up: `polls` polls of ~100 ns each; a negative value restores the default (2^26 polls, several
- * seconds).  Process-wide, read at each launch.  A short limit makes the step stop at its first
- * barrier with ssgi_step_fused_check reporting failure, as a stalled block would (a test of
- * the error path: the blocks return, nothing faults, and the next launch starts clean). */
+/* How long a block of later ssgi_step_fused launches waits for the previous phase before it
+ * gives up: `polls` polls of ~100 ns each; a negative value restores the default (2^26 polls,
+ * several seconds).  Process-wide, read at each launch.  A short limit makes the step stop at
+ * its first phase boundary with ssgi_step_fused_check reporting failure, as a stalled block
+ * would (a test of the error path: the blocks return, nothing faults, and the next launch
+ * starts clean). */
 ssgi_status ssgi_step_fused_set_wait_limit(int64_t polls);
-/* Synchronous: the durations (ns, from %globaltimer) of the last fused step's phases as seen by
- * its first block, in order: pyramids (env mips + Hi-Z, with the clears), direct shading,
- * trace + loss, Monte-Carlo adjoint, direct adjoint, mip-chain adjoint (the last is block 0's
- * own share only). */
+/* Synchronous: the durations (ns, from %globaltimer) of the last fused step's phases, each from
+ * its first block's start to its last block's end, in order: pyramids (env mips + Hi-Z, with
+ * the clears), direct shading, trace + loss, Monte-Carlo adjoint, direct adjoint, mip-chain
+ * adjoint. */
 #define SSGI_FUSED_PHASES 6
 ssgi_status ssgi_step_fused_phase_ns(const void *workspace, uint64_t *ns);
 

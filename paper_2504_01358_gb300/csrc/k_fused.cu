@@ -1,15 +1,25 @@
 // k_fused.cu -- one inverse-rendering step (all views of a frame: environment mips, Hi-Z,
-// direct shading, trace with stored hits, L2 loss, backward) in a single persistent launch.
+// direct shading, trace with stored hits, L2 loss, backward) in a single launch.
 //
-// The launch is cooperative, so every block is resident at once and the blocks may wait for
-// each other.  The step has five grid barriers, one per true all-to-all dependency:
-//   pyramids | shading | trace + loss | Monte-Carlo adjoint | direct adjoint | mip-chain adjoint
+// One block per work item, in phase order:
+//   clears | pyramids | shading | trace + loss | Monte-Carlo adjoint | direct adjoint | mip-chain adjoint
 // (shading reads any mip level; the trace reads any pixel's c1; the direct adjoint of a pixel
 // needs every receiver's scatter into its g_c1; the mip-chain adjoint needs every texel's
-// gradient).  Inside the pyramid phase the top levels are built by whichever block finishes
-// the last tile of a view (a counter, no waiting).  Work inside a phase is handed out from
-// counters, block by block.  The barrier is bounded: a block that waits longer than
-// kBarrierSpinLimit sleeps marks the error word and every block leaves; nothing spins forever.
+// gradient).  A block takes a ticket from a counter when it starts; the ticket names its phase
+// and item, so tickets go out in phase order.  Before working, a block of phase k waits until
+// every item of phase k - 1 has finished (a completion count per phase).  That wait always
+// ends: every item of phase k - 1 took its ticket earlier, so its block is already resident
+// and running (no cooperative launch and no residency limit is needed), and it waits only for
+// phase k - 2, which finished before.  The wait is still bounded: a block that polls longer than
+// the limit marks the error word and returns, and every later block sees the mark and returns;
+// nothing spins forever.  Inside the pyramid phase the top levels are built by whichever block
+// finishes the last tile of a pyramid (a counter, no waiting).
+//
+// Why not persistent blocks: the trace's tiles vary in cost by an order of magnitude, and
+// resident blocks that loop over tiles from a counter measured 12-21 % slower than the same
+// tiles as a grid of blocks (one per tile) that the hardware schedules; with one block per item
+// the trace phase keeps the grid's schedule.
+//
 // The per-item code is the stand-alone kernels' (ssgi_ops.cuh), so the results match the
 // per-stage path bit for bit (gradients up to the order of atomic additions).
 #include <algorithm>
@@ -20,25 +30,32 @@
 
 namespace ssgi {
 
-constexpr int kFusedThreads = 128;                // one 8 x 16 trace tile per block iteration
+constexpr int kFusedThreads = 128;                  // one 8 x 16 trace tile per block
 constexpr long long kBarrierSpinLimit = 1ll << 26;  // x ~100 ns sleeps: several seconds (default)
-constexpr int kFusedBarBytes = 512;               // control block at the start of the workspace
-constexpr int kFusedStampOffset = 256;            // bytes into it: 64-bit phase timestamps
+constexpr int kFusedBarBytes = 512;                 // control block at the start of the workspace
+constexpr int kFusedStampOffset = 256;              // bytes into it: 64-bit phase timestamps
+constexpr int kPhases = SSGI_FUSED_PHASES + 1;      // the clears, then the reported phases
+constexpr int kClearPerBlock = kFusedThreads * 32;  // float4s a clearing block zeroes
+// 128-pixel chunks per item in the per-pixel phases: items coarse enough that the per-item
+// ticket, wait and count stay small, fine enough to balance (the trace: one tile per item)
+constexpr int kShadeChunks = 1;  // shading, direct adjoint, mip-chain adjoint
+constexpr int kMcChunks = 1;     // Monte-Carlo adjoint (16-32 samples a pixel)
 
 // Control words (32-bit) of the control block.
 enum : int {
-  kArrive = 0,     // grid barrier: arrivals
-  kGen = 1,        // grid barrier: generation
-  kErr = 2,        // a block gave up waiting
-  kPyrNext = 3,    // next pyramid tile
-  kTraceNext = 4,  // next trace tile
-  kMcNext = 5,     // next Monte-Carlo adjoint chunk
-  kDirNext = 6,    // next direct adjoint chunk
-  kEnvDone = 7,    // environment tiles finished
-  kHizDone = 8,    // Hi-Z tiles finished, one word per view
+  kTicket = 0,                  // next ticket
+  kErr = 1,                     // a block gave up waiting
+  kEnvDone = 2,                 // environment tiles finished
+  kDone = 3,                    // kDone + k: finished items of phase k
+  kHizDone = kDone + kPhases,   // Hi-Z tiles finished, one word per view
 };
-static_assert((kHizDone + SSGI_MAX_VIEWS) * 4 <= kFusedStampOffset, "control words overlap the stamps");
-static_assert(kFusedStampOffset + 8 * (SSGI_FUSED_PHASES + 1) <= kFusedBarBytes, "stamps overflow");
+// the loss's FP64 accumulator (the trace's ~10^5 tiles each add a partial sum: in FP32 their
+// rounding would reach 1e-5 of the loss)
+constexpr int kLossAccOffset = 248;
+static_assert((kHizDone + SSGI_MAX_VIEWS) * 4 <= kLossAccOffset, "control words overlap the loss accumulator");
+static_assert(kLossAccOffset + 8 <= kFusedStampOffset, "the loss accumulator overlaps the stamps");
+// per phase: the start of its first item and the end of its last
+static_assert(kFusedStampOffset + 16 * kPhases <= kFusedBarBytes, "stamps overflow");
 
 struct FusedArgs {
   FrameArgs f;
@@ -50,7 +67,11 @@ struct FusedArgs {
   unsigned* ctl;     // workspace: control block
   long long n_gc1;   // float4s of g_c1
   int n_gmips;       // float4s of g_mips
-  long long wait_limit;  // polls a block makes at a grid barrier before it gives up
+  long long wait_limit;        // polls a block makes before it gives up
+  int items[kPhases];          // work items of each phase
+  int first[kPhases + 1];      // ticket of each phase's first item (prefix sums of items)
+  int hx, hy, ex, ey, n_hz;    // pyramid tiles: Hi-Z per view, environment, Hi-Z in all views
+  int tx, ty;                  // trace tiles (8 x 16) per view
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -59,25 +80,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Block 0 records when it leaves barrier `k` (slot 0 = its start): the phase durations.
-__device__ __forceinline__ void stamp(unsigned* ctl, int k) {
-  if (blockIdx.x == 0 && threadIdx.x == 0)
-    reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(ctl) + kFusedStampOffset)[k] = global_ns();
-}
-
-// Block-level dynamic work loop: the block takes chunk after chunk from `counter` (zero at the
-// start of the launch) until all `n` are taken; body(c) runs on every thread of the block.
-template <class Body>
-__device__ __forceinline__ void for_each_chunk(unsigned* counter, int n, Body body) {
-  __shared__ int s_c;
-  for (;;) {
-    if (threadIdx.x == 0) s_c = (int)atomicAdd(counter, 1u);
-    __syncthreads();
-    const int c = s_c;
-    __syncthreads();
-    if (c >= n) break;
-    body(c);
-  }
+__device__ __forceinline__ unsigned long long* stamps(unsigned* ctl) {
+  return reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(ctl) + kFusedStampOffset);
 }
 
 // Block-level: counts this block's finished piece of work on `counter`; true for the block that
@@ -93,153 +97,132 @@ __device__ __forceinline__ bool last_arrival(unsigned* counter, unsigned total) 
   return last;
 }
 
-// Grid barrier for a cooperative launch; returns false if any block gave up waiting (after
-// `limit` polls of ~100 ns each).
-__device__ __forceinline__ bool grid_sync(unsigned* ctl, long long limit) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* vgen = ctl + kGen;
-    volatile unsigned* verr = ctl + kErr;
-    const unsigned gen = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(ctl + kArrive, 1u) + 1u;
-    int ok = 1;
-    if (arrived == gridDim.x) {
-      atomicExch(ctl + kArrive, 0u);
-      __threadfence();
-      atomicAdd(const_cast<unsigned*>(vgen), 1u);
-    } else {
-      long long spins = 0;
-      while (*vgen == gen) {
-        if (*verr) {
-          ok = 0;
-          break;
-        }
-        if (++spins > limit) {
-          atomicExch(const_cast<unsigned*>(verr), 1u);
-          ok = 0;
-          break;
-        }
-        __nanosleep(100);
+// Thread 0: waits until phase ph - 1 has finished all its items.  false if a block gave up
+// (this one after `limit` polls of ~100 ns, or another one before).
+__device__ __forceinline__ bool wait_for_phase(const FusedArgs& F, int ph) {
+  volatile unsigned* err = F.ctl + kErr;
+  if (ph > 0) {
+    volatile unsigned* done = F.ctl + kDone + ph - 1;
+    const unsigned need = (unsigned)F.items[ph - 1];
+    long long spins = 0;
+    while (*done < need) {
+      if (*err) return false;
+      if (++spins > F.wait_limit) {
+        atomicExch(const_cast<unsigned*>(err), 1u);
+        return false;
       }
+      __nanosleep(100);
     }
-    __threadfence();
-    s_ok = ok && *verr == 0;
+    __threadfence();  // the finished phase's stores are visible to this block's loads
   }
-  __syncthreads();
-  return s_ok != 0;
+  return *err == 0;
 }
 
-// Sizes every phase needs, computed once per block into shared memory and read back inside
-// each phase: a read after a grid barrier (which synchronises the block) cannot be merged with
-// one before it, so no value stays in a register through the trace and adjoint loops.
-struct PhaseConsts {
-  long long HW, npx, gsz;
-  int V, H, W, nchunks;
-};
+// Block-level: this block's item of phase ph is done; the block that completes the phase
+// stamps its end (no contended atomics on the stamps).
+__device__ __forceinline__ void finish_item(const FusedArgs& F, int ph) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();  // the item's stores before its count
+    if (atomicAdd(F.ctl + kDone + ph, 1u) == (unsigned)F.items[ph] - 1u) stamps(F.ctl)[2 * ph + 1] = global_ns();
+  }
+}
 
-// Seven resident blocks per SM (72 registers a thread): fewer spills in the trace phase than at
-// eight blocks and 64 registers, which measured slower (as did six at 80).
+// One item per block.  Seven resident blocks per SM (72 registers a thread): fewer spills in the
+// trace than at eight blocks and 64 registers, which measured slower (as did six at 80).
 template <bool kCid, bool kPathwise>
 __global__ void __launch_bounds__(kFusedThreads, 7) k_step_fused(const __grid_constant__ FusedArgs F) {
   const FrameArgs& A = F.f;
-  const EnvInfo& e = A.e;
   __shared__ LevelTable s_lv;
   __shared__ TileBuf s_tile;
-  __shared__ PhaseConsts s_k;
+  __shared__ int s_phase, s_item, s_ok;
   if (threadIdx.x == 0) {
-    s_k.V = A.vs.V;
-    s_k.H = A.vs.H;
-    s_k.W = A.vs.W;
-    s_k.HW = (long long)A.vs.H * A.vs.W;
-    s_k.npx = s_k.V * s_k.HW;
-    s_k.gsz = (long long)gridDim.x * kFusedThreads;
-    s_k.nchunks = (int)((s_k.npx + kFusedThreads - 1) / kFusedThreads);
+    const int t = (int)atomicAdd(F.ctl + kTicket, 1u);
+    int ph = 0;
+    while (ph + 1 < kPhases && t >= F.first[ph + 1]) ++ph;
+    s_phase = ph;
+    s_item = t - F.first[ph];
+    s_ok = t < F.first[kPhases] && wait_for_phase(F, ph);
+    if (s_ok && s_item == 0) stamps(F.ctl)[2 * ph] = global_ns();  // the phase's first item
   }
   __syncthreads();
-  stamp(F.ctl, 0);
+  if (!s_ok) return;
+  const int ph = s_phase, item = s_item;
+  const long long HW = (long long)A.vs.H * A.vs.W, npx = A.vs.V * HW;
 
-  // P0: clear the backward accumulators and the loss; Hi-Z and environment pyramids, 32 x 32
-  // tiles through level 5, levels 6.. by the block that finishes a pyramid's last tile.
-  {
-    const long long gtid = (long long)blockIdx.x * kFusedThreads + threadIdx.x, gsz = s_k.gsz;
-    const int V = s_k.V, H = s_k.H, W = s_k.W;
-    for (long long i = gtid; i < F.n_gc1; i += gsz) A.g_c1[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (long long i = gtid; i < F.n_gmips; i += gsz) A.g_mips[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (gtid == 0) *F.loss = 0.0f;
-    const int hx = (W + kHizTile - 1) / kHizTile, hy = (H + kHizTile - 1) / kHizTile;
-    const int n_hz = A.levels > 1 ? hx * hy * V : 0;
-    const int ex = e.w[0] / min(kHizTile, e.w[0]), ey = e.h[0] / min(kHizTile, e.h[0]);
-    for_each_chunk(F.ctl + kPyrNext, n_hz + ex * ey, [&](int t) {
-      if (t < n_hz) {
-        const int v = t / (hx * hy), r = t - v * hx * hy;
-        hiz_tile_block(A.depth, H, W, A.hz, F.hiz, v, r % hx, r / hx, s_tile);
-        if (A.levels > 6 && last_arrival(F.ctl + kHizDone + v, hx * hy)) hiz_upper_block(A.hz, v, F.hiz);
-      } else {
-        const int r = t - n_hz;
-        env_tile_block(F.env, e, F.mips, r % ex, r / ex, s_tile);
-        if (e.levels > 6 && last_arrival(F.ctl + kEnvDone, ex * ey)) env_upper_block(e, F.mips);
-      }
-    });
-  }
-  if (!grid_sync(F.ctl, F.wait_limit)) return;
-  stamp(F.ctl, 1);
-
-  // P1: direct shading
-  {
-    const long long npx = s_k.npx, gsz = s_k.gsz;
-    for (long long p = (long long)blockIdx.x * kFusedThreads + threadIdx.x; p < npx; p += gsz) shade_pixel(A, p);
-  }
-  if (!grid_sync(F.ctl, F.wait_limit)) return;
-  stamp(F.ctl, 2);
-
-  // P2: trace, one 8 x 16 tile per block iteration, and the L2 loss of each finished pixel.
-  // The per-tile cost varies by an order of magnitude (sky vs. rays that run out of steps),
-  // so blocks take the next tile from a counter instead of a fixed stride.
-  {
+  if (ph == 0) {
+    // the backward's accumulators and the loss
+    const long long base = (long long)item * kClearPerBlock + threadIdx.x;
+    for (int k = 0; k < kClearPerBlock / kFusedThreads; ++k) {
+      const long long i = base + (long long)k * kFusedThreads;
+      if (i < F.n_gc1) A.g_c1[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      else if (i - F.n_gc1 < F.n_gmips) A.g_mips[i - F.n_gc1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (item == 0 && threadIdx.x == 0) *F.loss = 0.0f;  // written again by the adjoint's first item
+  } else if (ph == 1) {
+    // Hi-Z and environment pyramids: 32 x 32 tiles through level 5, levels 6.. by the block
+    // that finishes a pyramid's last tile
+    const EnvInfo& e = A.e;
+    if (item < F.n_hz) {
+      const int v = item / (F.hx * F.hy), r = item - v * F.hx * F.hy;
+      hiz_tile_block(A.depth, A.vs.H, A.vs.W, A.hz, F.hiz, v, r % F.hx, r / F.hx, s_tile);
+      if (A.levels > 6 && last_arrival(F.ctl + kHizDone + v, F.hx * F.hy)) hiz_upper_block(A.hz, v, F.hiz);
+    } else {
+      const int r = item - F.n_hz;
+      env_tile_block(F.env, e, F.mips, r % F.ex, r / F.ex, s_tile);
+      if (e.levels > 6 && last_arrival(F.ctl + kEnvDone, F.ex * F.ey)) env_upper_block(e, F.mips);
+    }
+  } else if (ph == 2) {
+    for (int c = item * kShadeChunks; c < (item + 1) * kShadeChunks; ++c) {
+      const long long p = (long long)c * kFusedThreads + threadIdx.x;
+      if (p < npx) shade_pixel(A, p);
+    }
+  } else if (ph == 3) {
+    // trace one 8 x 16 tile and the L2 loss of its pixels
+    const int v = item / (F.tx * F.ty), r = item - v * F.tx * F.ty;
+    const int x = (r % F.tx) * 8 + (threadIdx.x % 8), y = (r / F.tx) * 16 + (threadIdx.x / 8);
+    fill_levels(A, v, s_lv);
+    __syncthreads();
     float acc = 0.0f;
-    const int tx = (s_k.W + 7) / 8, ty = (s_k.H + 15) / 16;
-    for_each_chunk(F.ctl + kTraceNext, tx * ty * s_k.V, [&](int t) {
-      const int v = t / (tx * ty), r = t - v * tx * ty;
-      const int x = (r % tx) * 8 + (threadIdx.x % 8), y = (r / tx) * 16 + (threadIdx.x / 8);
-      fill_levels(A, v, s_lv);  // the previous tile's reads ended at for_each_chunk's barriers
-      __syncthreads();
-      if (x < s_k.W && y < s_k.H) {
-        const float3 fin = trace_pixel<kCid>(A, x, y, v, s_lv);
-        const long long p = v * s_k.HW + (long long)y * s_k.W + x;
-        const float inv = 1.0f / (float)(s_k.npx * 3);
-        acc += (A.flags & SSGI_SRGB_LOSS) ? l2_srgb_pixel(A, p, fin, inv) : l2_pixel(A, p, fin, inv);
-      }
-    });
-    block_sum_add(acc, F.loss, 1.0f / (float)(s_k.npx * 3));
+    const float inv = 1.0f / (float)(npx * 3);
+    if (x < A.vs.W && y < A.vs.H) {
+      const float3 fin = trace_pixel<kCid>(A, x, y, v, s_lv);
+      const long long p = v * HW + (long long)y * A.vs.W + x;
+      acc = (A.flags & SSGI_SRGB_LOSS) ? l2_srgb_pixel(A, p, fin, inv) : l2_pixel(A, p, fin, inv);
+    }
+    // the tile's partial sum into the FP64 accumulator (zeroed with the control block)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ float part[kFusedThreads / 32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int k = 0; k < kFusedThreads / 32; ++k) sum += (double)part[k];
+      atomicAdd(reinterpret_cast<double*>(reinterpret_cast<char*>(F.ctl) + kLossAccOffset), sum);
+    }
+  } else if (ph == 4) {
+    // Monte-Carlo adjoint (scatters into g_c1 and g_mips); its first item also writes the loss,
+    // which every trace tile has added to by now
+    if (item == 0 && threadIdx.x == 0)
+      *F.loss = (float)(*reinterpret_cast<volatile double*>(reinterpret_cast<char*>(F.ctl) + kLossAccOffset) / (3.0 * (double)npx));
+    for (int c = item * kMcChunks; c < (item + 1) * kMcChunks; ++c) {
+      const long long p = (long long)c * kFusedThreads + threadIdx.x;
+      if (p < npx) bwd_mc_pixel<kPathwise>(A, p);
+    }
+  } else if (ph == 5) {
+    for (int c = item * kShadeChunks; c < (item + 1) * kShadeChunks; ++c) {
+      const long long p = (long long)c * kFusedThreads + threadIdx.x;
+      if (p < npx) bwd_direct_pixel(A, p);
+    }
+  } else {
+    // mip-chain adjoint to the base texels
+    for (int c = item * kShadeChunks; c < (item + 1) * kShadeChunks; ++c) {
+      const int t = c * kFusedThreads + threadIdx.x;
+      if (t < A.e.h[0] * A.e.w[0] * 3) bwd_env_item(A.e, A.g_mips, F.g_env, t);
+    }
   }
-  if (!grid_sync(F.ctl, F.wait_limit)) return;
-  stamp(F.ctl, 3);
-
-  // P3: Monte-Carlo adjoint (scatters into g_c1 and g_mips)
-  for_each_chunk(F.ctl + kMcNext, s_k.nchunks, [&](int c) {
-    const long long p = (long long)c * kFusedThreads + threadIdx.x;
-    if (p < s_k.npx) bwd_mc_pixel<kPathwise>(A, p);
-  });
-  if (!grid_sync(F.ctl, F.wait_limit)) return;
-  stamp(F.ctl, 4);
-
-  // P4: direct-shading adjoint
-  for_each_chunk(F.ctl + kDirNext, s_k.nchunks, [&](int c) {
-    const long long p = (long long)c * kFusedThreads + threadIdx.x;
-    if (p < s_k.npx) bwd_direct_pixel(A, p);
-  });
-  if (!grid_sync(F.ctl, F.wait_limit)) return;
-  stamp(F.ctl, 5);
-
-  // P5: mip-chain adjoint to the base texels
-  {
-    const long long gsz = s_k.gsz, n = (long long)e.h[0] * e.w[0] * 3;
-    for (long long t = (long long)blockIdx.x * kFusedThreads + threadIdx.x; t < n; t += gsz)
-      bwd_env_item(e, A.g_mips, F.g_env, (int)t);
-  }
-  stamp(F.ctl, 6);
+  finish_item(F, ph);
 }
 
 struct FusedLayout {
@@ -343,26 +326,35 @@ ssgi_status ssgi_step_fused(const ssgi_gbuffer* g, const ssgi_camera* cams, cons
   A.seed = p->seed;
   A.flags = p->flags;
 
-  int dev = 0, sms = 0, coop = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess)
-    return SSGI_ERR_CUDA;
-  if (!coop) return SSGI_ERR_UNSUPPORTED;
+  const long long nch = (npx + kFusedThreads - 1) / kFusedThreads;
+  const int H = g->d.height, W = g->d.width, V = g->d.views;
+  F.hx = (W + kHizTile - 1) / kHizTile;
+  F.hy = (H + kHizTile - 1) / kHizTile;
+  F.n_hz = p->hiz_levels > 1 ? F.hx * F.hy * V : 0;
+  F.ex = env_w / std::min(kHizTile, env_w);
+  F.ey = env_h / std::min(kHizTile, env_h);
+  F.tx = (W + 7) / 8;
+  F.ty = (H + 15) / 16;
+  const long long clear = (F.n_gc1 + F.n_gmips + kClearPerBlock - 1) / kClearPerBlock;
+  const long long nenv = ((long long)env_h * env_w * 3 + kFusedThreads - 1) / kFusedThreads;
+  const long long items[kPhases] = {clear, (long long)F.n_hz + F.ex * F.ey, (nch + kShadeChunks - 1) / kShadeChunks,
+                                    (long long)F.tx * F.ty * V, (nch + kMcChunks - 1) / kMcChunks,
+                                    (nch + kShadeChunks - 1) / kShadeChunks, (nenv + kShadeChunks - 1) / kShadeChunks};
+  long long total = 0;
+  for (int k = 0; k < kPhases; ++k) {
+    F.first[k] = (int)total;
+    F.items[k] = (int)items[k];
+    total += items[k];
+  }
+  if (total >= (1ll << 31)) return SSGI_ERR_UNSUPPORTED;
+  F.first[kPhases] = (int)total;
   const bool cid = (p->flags & SSGI_DIFFUSE_INDIRECT) != 0, pw = (p->flags & SSGI_PATHWISE) != 0;
-  const void* fn = cid ? (pw ? (const void*)k_step_fused<true, true> : (const void*)k_step_fused<true, false>)
-                       : (pw ? (const void*)k_step_fused<false, true> : (const void*)k_step_fused<false, false>);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kFusedThreads, 0) != cudaSuccess || per_sm < 1)
-    return SSGI_ERR_CUDA;
-  const int blocks = per_sm * sms;
+  auto fn = cid ? (pw ? k_step_fused<true, true> : k_step_fused<true, false>)
+                : (pw ? k_step_fused<false, true> : k_step_fused<false, false>);
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemsetAsync(ws + L.bar, 0, kFusedBarBytes, s) != cudaSuccess) return SSGI_ERR_CUDA;
-  void* args[] = {(void*)&F};
-  if (cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(kFusedThreads), args, 0, s) != cudaSuccess) {
-    cudaGetLastError();
-    return SSGI_ERR_CUDA;
-  }
-  return SSGI_OK;
+  fn<<<(unsigned)total, kFusedThreads, 0, s>>>(F);
+  return launch_status();
 }
 
 ssgi_status ssgi_step_fused_check(const void* workspace, int32_t* failed) {
@@ -375,10 +367,15 @@ ssgi_status ssgi_step_fused_check(const void* workspace, int32_t* failed) {
 
 ssgi_status ssgi_step_fused_phase_ns(const void* workspace, uint64_t* ns) {
   if (!workspace || !ns) return SSGI_ERR_INVALID_ARG;
-  unsigned long long t[SSGI_FUSED_PHASES + 1];
+  unsigned long long t[2 * kPhases];
   if (cudaMemcpy(t, (const char*)workspace + kFusedStampOffset, sizeof(t), cudaMemcpyDeviceToHost) != cudaSuccess)
     return SSGI_ERR_CUDA;
-  for (int k = 0; k < SSGI_FUSED_PHASES; ++k) ns[k] = t[k + 1] >= t[k] ? t[k + 1] - t[k] : 0;
+  // phase k (after the clears): from its first block's start to its last block's end; the
+  // pyramids' span starts with the clears
+  for (int k = 0; k < SSGI_FUSED_PHASES; ++k) {
+    const unsigned long long start = t[2 * (k == 0 ? 0 : k + 1)], end = t[2 * (k + 1) + 1];
+    ns[k] = end >= start ? end - start : 0;
+  }
   return SSGI_OK;
 }
 

@@ -274,14 +274,14 @@ def ssgi_step_fused(g: GBuffer, cams, env: torch.Tensor, lut: torch.Tensor, targ
 
 
 def ssgi_step_fused_check(workspace: torch.Tensor) -> bool:
-    """True if the last fused step on this workspace stopped at a grid barrier (synchronous)."""
+    """True if a block of the last fused step on this workspace gave up waiting (synchronous)."""
     f = C.c_int32()
     N.call("ssgi_step_fused_check", _dev(workspace, "workspace", torch.uint8), C.byref(f))
     return bool(f.value)
 
 
 def ssgi_step_fused_set_wait_limit(polls: int) -> None:
-    """Polls (~100 ns each) a fused-step block waits at a grid barrier before giving up; < 0: default."""
+    """Polls (~100 ns each) a fused-step block waits for the previous phase before giving up; < 0: default."""
     N.call("ssgi_step_fused_set_wait_limit", int(polls))
 
 

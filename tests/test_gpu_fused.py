@@ -1,5 +1,5 @@
-"""The fused persistent step (ssgi_step_fused: all stages of a multi-view inverse-rendering step
-in one cooperative launch) against the per-stage calls and the FP64 oracle."""
+"""The fused step (ssgi_step_fused: all stages of a multi-view inverse-rendering step
+in one launch) against the per-stage calls and the FP64 oracle."""
 import numpy as np
 import pytest
 import torch
@@ -84,9 +84,9 @@ def test_config4_eight_views_fused_against_per_stage_and_oracle():
     assert (sub["hit_idx"] >= 0).mean() > 0.02
 
 
-def test_fused_barrier_gives_up_and_the_next_step_is_clean():
-    """The grid barrier's bounded wait: with the wait limit at 0 polls a block that reaches a
-    barrier before the others gives up at once, marks the error word and every block returns
+def test_fused_phase_wait_gives_up_and_the_next_step_is_clean():
+    """The phase boundary's bounded wait: with the wait limit at 0 polls a block whose previous
+    phase has not finished gives up at once, marks the error word, and every later block returns
     (no hang, no fault); ssgi_step_fused_check reports it.  With the default limit restored the
     next launch on the same workspace runs to the end and equals the per-stage path."""
     import paper_2504_01358_gb300 as S
