@@ -30,7 +30,7 @@
 
 namespace ssgi {
 
-constexpr int kFusedThreads = 128;                  // one 8 x 16 trace tile per block
+constexpr int kFusedThreads = 128;                  // one 16 x 8 trace tile per block
 constexpr long long kBarrierSpinLimit = 1ll << 26;  // x ~100 ns sleeps: several seconds (default)
 constexpr int kFusedBarBytes = 512;                 // control block at the start of the workspace
 constexpr int kFusedStampOffset = 256;              // bytes into it: 64-bit phase timestamps
@@ -71,7 +71,7 @@ struct FusedArgs {
   int items[kPhases];          // work items of each phase
   int first[kPhases + 1];      // ticket of each phase's first item (prefix sums of items)
   int hx, hy, ex, ey, n_hz;    // pyramid tiles: Hi-Z per view, environment, Hi-Z in all views
-  int tx, ty;                  // trace tiles (8 x 16) per view
+  int tx, ty;                  // trace tiles (16 x 8) per view
 };
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -178,9 +178,9 @@ __global__ void __launch_bounds__(kFusedThreads, 7) k_step_fused(const __grid_co
       if (p < npx) shade_pixel(A, p);
     }
   } else if (ph == 3) {
-    // trace one 8 x 16 tile and the L2 loss of its pixels
+    // trace one 16 x 8 tile (16 x 2 per warp, as k_trace) and the L2 loss of its pixels
     const int v = item / (F.tx * F.ty), r = item - v * F.tx * F.ty;
-    const int x = (r % F.tx) * 8 + (threadIdx.x % 8), y = (r / F.tx) * 16 + (threadIdx.x / 8);
+    const int x = (r % F.tx) * 16 + (threadIdx.x % 16), y = (r / F.tx) * 8 + (threadIdx.x / 16);
     fill_levels(A, v, s_lv);
     __syncthreads();
     float acc = 0.0f;
@@ -333,8 +333,8 @@ ssgi_status ssgi_step_fused(const ssgi_gbuffer* g, const ssgi_camera* cams, cons
   F.n_hz = p->hiz_levels > 1 ? F.hx * F.hy * V : 0;
   F.ex = env_w / std::min(kHizTile, env_w);
   F.ey = env_h / std::min(kHizTile, env_h);
-  F.tx = (W + 7) / 8;
-  F.ty = (H + 15) / 16;
+  F.tx = (W + 15) / 16;
+  F.ty = (H + 7) / 8;
   const long long clear = (F.n_gc1 + F.n_gmips + kClearPerBlock - 1) / kClearPerBlock;
   const long long nenv = ((long long)env_h * env_w * 3 + kFusedThreads - 1) / kFusedThreads;
   const long long items[kPhases] = {clear, (long long)F.n_hz + F.ex * F.ey, (nch + kShadeChunks - 1) / kShadeChunks,
