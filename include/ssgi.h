@@ -221,9 +221,10 @@ ssgi_status ssgi_backward(const float *g_final, const ssgi_gbuffer *g, const ssg
 /* Fused inverse-rendering step: every stage above for all views of a frame in ONE launch     */
 /* (env mips, Hi-Z, direct shading, trace with stored hits, L2 loss against `target`,         */
 /* backward): one block per work item, phase after phase, each block of a phase waiting       */
-/* (bounded) until the previous phase has finished.  Same per-item code as the separate calls, */
-/* so final and hit_idx equal theirs bit for bit and the gradients agree up to the order of    */
-/* atomic additions.                                                                          */
+/* (bounded) until the previous phase has finished; a trace tile's block also runs the        */
+/* Monte-Carlo adjoint of its pixels.  Same per-pixel code as the separate calls, so final    */
+/* and hit_idx equal theirs bit for bit and the gradients agree up to the order of atomic     */
+/* additions.                                                                                 */
 /* ---------------------------------------------------------------------------------------- */
 /* workspace bytes of ssgi_step_fused (mips, pyramid, c_d, c1, g_final and the backward scratch) */
 size_t ssgi_step_fused_workspace_bytes(ssgi_dims d, int32_t env_h, int32_t env_w, int32_t hiz_levels);
@@ -248,9 +249,9 @@ ssgi_status ssgi_step_fused_check(const void *workspace, int32_t *failed);
 ssgi_status ssgi_step_fused_set_wait_limit(int64_t polls);
 /* Synchronous: the durations (ns, from %globaltimer) of the last fused step's phases, each from
  * its first block's start to its last block's end, in order: pyramids (env mips + Hi-Z, with
- * the clears), direct shading, trace + loss, Monte-Carlo adjoint, direct adjoint, mip-chain
+ * the clears), direct shading, trace + loss + Monte-Carlo adjoint, direct adjoint, mip-chain
  * adjoint. */
-#define SSGI_FUSED_PHASES 6
+#define SSGI_FUSED_PHASES 5
 ssgi_status ssgi_step_fused_phase_ns(const void *workspace, uint64_t *ns);
 
 /* ---------------------------------------------------------------------------------------- */

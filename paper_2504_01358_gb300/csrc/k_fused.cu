@@ -2,10 +2,12 @@
 // direct shading, trace with stored hits, L2 loss, backward) in a single launch.
 //
 // One block per work item, in phase order:
-//   clears | pyramids | shading | trace + loss | Monte-Carlo adjoint | direct adjoint | mip-chain adjoint
+//   clears | pyramids | shading | trace + loss + Monte-Carlo adjoint | direct adjoint | mip-chain adjoint
 // (shading reads any mip level; the trace reads any pixel's c1; the direct adjoint of a pixel
 // needs every receiver's scatter into its g_c1; the mip-chain adjoint needs every texel's
-// gradient).  A block takes a ticket from a counter when it starts; the ticket names its phase
+// gradient).  The Monte-Carlo adjoint of a pixel needs only that pixel's hits and dL/dfinal
+// (the loss is a sum over pixels), so the block that traces a tile goes on to its adjoint: the
+// scatter of one tile overlaps the march of the others, and no phase boundary separates them.  A block takes a ticket from a counter when it starts; the ticket names its phase
 // and item, so tickets go out in phase order.  Before working, a block of phase k waits until
 // every item of phase k - 1 has finished (a completion count per phase).  That wait always
 // ends: every item of phase k - 1 took its ticket earlier, so its block is already resident
@@ -21,7 +23,11 @@
 // the trace phase keeps the grid's schedule.
 //
 // The per-item code is the stand-alone kernels' (ssgi_ops.cuh), so the results match the
-// per-stage path bit for bit (gradients up to the order of atomic additions).
+// per-stage path bit for bit (gradients up to the order of atomic additions).  Data another
+// block wrote earlier in the launch is read through L2 (ld.global.cg) where some block may have
+// cached those lines before they were written; c1, the mip chain and the pyramid are read
+// through the read-only path only in phases after the one that writes them, which reads none of
+// them.
 #include <algorithm>
 #include <atomic>
 #include <cstring>
@@ -36,10 +42,9 @@ constexpr int kFusedBarBytes = 512;                 // control block at the star
 constexpr int kFusedStampOffset = 256;              // bytes into it: 64-bit phase timestamps
 constexpr int kPhases = SSGI_FUSED_PHASES + 1;      // the clears, then the reported phases
 constexpr int kClearPerBlock = kFusedThreads * 32;  // float4s a clearing block zeroes
-// 128-pixel chunks per item in the per-pixel phases: items coarse enough that the per-item
-// ticket, wait and count stay small, fine enough to balance (the trace: one tile per item)
+// 128-pixel chunks per item in the per-pixel phases (the trace: one tile per item); coarser
+// items measured slower
 constexpr int kShadeChunks = 1;  // shading, direct adjoint, mip-chain adjoint
-constexpr int kMcChunks = 1;     // Monte-Carlo adjoint (16-32 samples a pixel)
 
 // Control words (32-bit) of the control block.
 enum : int {
@@ -178,7 +183,8 @@ __global__ void __launch_bounds__(kFusedThreads, 7) k_step_fused(const __grid_co
       if (p < npx) shade_pixel(A, p);
     }
   } else if (ph == 3) {
-    // trace one 16 x 8 tile (16 x 2 per warp, as k_trace) and the L2 loss of its pixels
+    // trace one 16 x 8 tile (16 x 2 per warp, as k_trace), the L2 loss of its pixels and their
+    // Monte-Carlo adjoint (each thread's own pixel: its hits and dL/dfinal are this thread's)
     const int v = item / (F.tx * F.ty), r = item - v * F.tx * F.ty;
     const int x = (r % F.tx) * 16 + (threadIdx.x % 16), y = (r / F.tx) * 8 + (threadIdx.x / 16);
     fill_levels(A, v, s_lv);
@@ -188,7 +194,9 @@ __global__ void __launch_bounds__(kFusedThreads, 7) k_step_fused(const __grid_co
     if (x < A.vs.W && y < A.vs.H) {
       const float3 fin = trace_pixel<kCid>(A, x, y, v, s_lv);
       const long long p = v * HW + (long long)y * A.vs.W + x;
-      acc = (A.flags & SSGI_SRGB_LOSS) ? l2_srgb_pixel(A, p, fin, inv) : l2_pixel(A, p, fin, inv);
+      float3 gfin;
+      acc = (A.flags & SSGI_SRGB_LOSS) ? l2_srgb_pixel(A, p, fin, inv, gfin) : l2_pixel(A, p, fin, inv, gfin);
+      bwd_mc_pixel<kPathwise, true>(A, p, gfin);
     }
     // the tile's partial sum into the FP64 accumulator (zeroed with the control block)
 #pragma unroll
@@ -202,15 +210,10 @@ __global__ void __launch_bounds__(kFusedThreads, 7) k_step_fused(const __grid_co
       atomicAdd(reinterpret_cast<double*>(reinterpret_cast<char*>(F.ctl) + kLossAccOffset), sum);
     }
   } else if (ph == 4) {
-    // Monte-Carlo adjoint (scatters into g_c1 and g_mips); its first item also writes the loss,
-    // which every trace tile has added to by now
+    // direct adjoint; its first item also writes the loss, which every trace tile has added to
+    // by now
     if (item == 0 && threadIdx.x == 0)
       *F.loss = (float)(*reinterpret_cast<volatile double*>(reinterpret_cast<char*>(F.ctl) + kLossAccOffset) / (3.0 * (double)npx));
-    for (int c = item * kMcChunks; c < (item + 1) * kMcChunks; ++c) {
-      const long long p = (long long)c * kFusedThreads + threadIdx.x;
-      if (p < npx) bwd_mc_pixel<kPathwise>(A, p);
-    }
-  } else if (ph == 5) {
     for (int c = item * kShadeChunks; c < (item + 1) * kShadeChunks; ++c) {
       const long long p = (long long)c * kFusedThreads + threadIdx.x;
       if (p < npx) bwd_direct_pixel(A, p);
@@ -338,8 +341,8 @@ ssgi_status ssgi_step_fused(const ssgi_gbuffer* g, const ssgi_camera* cams, cons
   const long long clear = (F.n_gc1 + F.n_gmips + kClearPerBlock - 1) / kClearPerBlock;
   const long long nenv = ((long long)env_h * env_w * 3 + kFusedThreads - 1) / kFusedThreads;
   const long long items[kPhases] = {clear, (long long)F.n_hz + F.ex * F.ey, (nch + kShadeChunks - 1) / kShadeChunks,
-                                    (long long)F.tx * F.ty * V, (nch + kMcChunks - 1) / kMcChunks,
-                                    (nch + kShadeChunks - 1) / kShadeChunks, (nenv + kShadeChunks - 1) / kShadeChunks};
+                                    (long long)F.tx * F.ty * V, (nch + kShadeChunks - 1) / kShadeChunks,
+                                    (nenv + kShadeChunks - 1) / kShadeChunks};
   long long total = 0;
   for (int k = 0; k < kPhases; ++k) {
     F.first[k] = (int)total;

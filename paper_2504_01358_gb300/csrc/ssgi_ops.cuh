@@ -605,8 +605,10 @@ __device__ __forceinline__ float3 env_lookup_adj(const float* __restrict__ mips,
 // pdf frozen; d/d{n, rho} of f_s (n.w) / p_frozen).  kPathwise = true: the direction is a
 // function of (n, rho) at frozen uniforms (ggx_sample_h_jac), the weight is the cancelled
 // F G1 G1 (v.h) / ((n.v)(n.h)) and a miss's radiance follows the direction through the map.
-template <bool kPathwise>
-__device__ __forceinline__ void bwd_mc_pixel(const FrameArgs& A, long long p) {
+// kOwn: the calling thread traced this pixel itself (the fused step's trace item), so its hit
+// indices are read with ordinary loads (not the read-only path) and dL/dfinal comes in g_own.
+template <bool kPathwise, bool kOwn = false>
+__device__ __forceinline__ void bwd_mc_pixel(const FrameArgs& A, long long p, float3 g_own = float3{}) {
   const long long HW = (long long)A.vs.H * A.vs.W;
   const int view = (int)(p / HW);
   const int rem = (int)(p - view * HW);
@@ -623,7 +625,7 @@ __device__ __forceinline__ void bwd_mc_pixel(const FrameArgs& A, long long p) {
     const float rho = __ldg(A.rough + p), m = __ldg(A.metal + p);
     const float3 a = ld3(A.albedo + 3 * p);
     const float3 F0 = f3(f0_of(a.x, m), f0_of(a.y, m), f0_of(a.z, m));
-    const float3 gC = ld3(A.g_final + 3 * p) * (1.0f / (float)A.spp);
+    const float3 gC = (kOwn ? g_own : ld3(A.g_final + 3 * p)) * (1.0f / (float)A.spp);
     const float g1v = ggx_G1(nv, rho);
     float dgv_z, dgv_r;
     dlnG1(nv, rho, dgv_z, dgv_r);
@@ -631,7 +633,7 @@ __device__ __forceinline__ void bwd_mc_pixel(const FrameArgs& A, long long p) {
     for (int s = 0; s < A.spp; ++s) {
       const float2 xi = sample_uniforms(A.seed, view, (uint32_t)rem, (uint32_t)s);
       const Sample sm = make_sample(n, v, nv, rho, xi);
-      const int q = __ldg(A.hit_idx + p * A.spp + s);
+      const int q = kOwn ? A.hit_idx[p * A.spp + s] : __ldg(A.hit_idx + p * A.spp + s);
       // the forward's verdict on validity decides (n.v and n.w here may round differently)
       if (!sm.valid || q == SSGI_HIT_INVALID) continue;
       if (q >= HW) continue;  // not an index this G-buffer's trace can produce
@@ -803,11 +805,13 @@ __device__ __forceinline__ void block_sum_add(float acc, float* out, float scale
   __syncthreads();
 }
 
-// The L2 loss term of one pixel's final colour (already in registers); returns |r|^2.
-__device__ __forceinline__ float l2_pixel(const FrameArgs& A, long long p, float3 fin, float inv) {
+// The L2 loss term of one pixel's final colour (already in registers); returns |r|^2 and
+// stores g = dL/dfinal (also returned in g).
+__device__ __forceinline__ float l2_pixel(const FrameArgs& A, long long p, float3 fin, float inv, float3& g) {
   const float3 t = ld3(A.target + 3 * p);
   const float rx = fin.x - t.x, ry = fin.y - t.y, rz = fin.z - t.z;
-  st3(A.g_final + 3 * p, f3(2.0f * rx * inv, 2.0f * ry * inv, 2.0f * rz * inv));
+  g = f3(2.0f * rx * inv, 2.0f * ry * inv, 2.0f * rz * inv);
+  st3(A.g_final + 3 * p, g);
   return rx * rx + ry * ry + rz * rz;
 }
 
@@ -849,12 +853,14 @@ __device__ __forceinline__ void l2_block_vec(const float* __restrict__ f, const 
   block_sum_add(acc, loss, inv);
 }
 
-// The sRGB loss term of one pixel's final colour in registers; returns |r|^2.
-__device__ __forceinline__ float l2_srgb_pixel(const FrameArgs& A, long long p, float3 fin, float inv) {
+// The sRGB loss term of one pixel's final colour in registers; returns |r|^2 and stores (and
+// returns in g) dL/dfinal.
+__device__ __forceinline__ float l2_srgb_pixel(const FrameArgs& A, long long p, float3 fin, float inv, float3& g) {
   const float3 t = ld3(A.target + 3 * p);
   const float rx = tonemap_srgb(fin.x) - t.x, ry = tonemap_srgb(fin.y) - t.y, rz = tonemap_srgb(fin.z) - t.z;
-  st3(A.g_final + 3 * p, f3(2.0f * rx * tonemap_srgb_slope(fin.x) * inv, 2.0f * ry * tonemap_srgb_slope(fin.y) * inv,
-                            2.0f * rz * tonemap_srgb_slope(fin.z) * inv));
+  g = f3(2.0f * rx * tonemap_srgb_slope(fin.x) * inv, 2.0f * ry * tonemap_srgb_slope(fin.y) * inv,
+         2.0f * rz * tonemap_srgb_slope(fin.z) * inv);
+  st3(A.g_final + 3 * p, g);
   return rx * rx + ry * ry + rz * rz;
 }
 

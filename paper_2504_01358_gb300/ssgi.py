@@ -285,7 +285,7 @@ def ssgi_step_fused_set_wait_limit(polls: int) -> None:
     N.call("ssgi_step_fused_set_wait_limit", int(polls))
 
 
-FUSED_PHASES = ("pyramids", "shade", "trace_loss", "bwd_mc", "bwd_direct", "bwd_env")
+FUSED_PHASES = ("pyramids", "shade", "trace_loss_mc", "bwd_direct", "bwd_env")
 
 
 def ssgi_step_fused_phase_ns(workspace: torch.Tensor) -> dict:
