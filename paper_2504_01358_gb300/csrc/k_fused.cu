@@ -42,6 +42,15 @@ constexpr int kFusedBarBytes = 512;                 // control block at the star
 constexpr int kFusedStampOffset = 256;              // bytes into it: 64-bit phase timestamps
 constexpr int kPhases = SSGI_FUSED_PHASES + 1;      // the clears, then the reported phases
 constexpr int kClearPerBlock = kFusedThreads * 32;  // float4s a clearing block zeroes
+// Pyramid tiles: 16 x 16 (levels 1..4), an item covering 2 x 2 of them (the stand-alone
+// builder's 32 x 32 footprint); the levels above 4 are built by the block that finishes a
+// pyramid's last item.  The tile buffer (1 KB) shares shared memory with the trace's level table,
+// so seven blocks need at most 16 KB of shared memory and the rest of the SM's 256 KB stays L1
+// for the march: with a 32 x 32 tile (4 KB) the carve-out became 64 KB and the trace phase ran
+// 7 % slower (the stand-alone trace forced to that carve-out slows the same).
+constexpr int kFusedTile = 16;
+constexpr int kFusedTileLevels = tile_levels<kFusedTile>();
+constexpr int kFusedRegion = 2 * kFusedTile;
 // 128-pixel chunks per item in the per-pixel phases (the trace: one tile per item); coarser
 // items measured slower
 constexpr int kShadeChunks = 1;  // shading, direct adjoint, mip-chain adjoint
@@ -75,7 +84,7 @@ struct FusedArgs {
   long long wait_limit;        // polls a block makes before it gives up
   int items[kPhases];          // work items of each phase
   int first[kPhases + 1];      // ticket of each phase's first item (prefix sums of items)
-  int hx, hy, ex, ey, n_hz;    // pyramid tiles: Hi-Z per view, environment, Hi-Z in all views
+  int hx, hy, ex, ey, n_hz;    // pyramid items: Hi-Z regions per view, environment tiles, Hi-Z items in all views
   int tx, ty;                  // trace tiles (16 x 8) per view
 };
 
@@ -138,8 +147,10 @@ __device__ __forceinline__ void finish_item(const FusedArgs& F, int ph) {
 template <bool kCid, bool kPathwise>
 __global__ void __launch_bounds__(kFusedThreads, 7) k_step_fused(const __grid_constant__ FusedArgs F) {
   const FrameArgs& A = F.f;
-  __shared__ LevelTable s_lv;
-  __shared__ TileBuf s_tile;
+  __shared__ union {
+    LevelTable lv;                  // trace items
+    TileBufT<kFusedTile> tile;      // pyramid items
+  } s_u;
   __shared__ int s_phase, s_item, s_ok;
   if (threadIdx.x == 0) {
     const int t = (int)atomicAdd(F.ctl + kTicket, 1u);
@@ -165,17 +176,23 @@ __global__ void __launch_bounds__(kFusedThreads, 7) k_step_fused(const __grid_co
     }
     if (item == 0 && threadIdx.x == 0) *F.loss = 0.0f;  // written again by the adjoint's first item
   } else if (ph == 1) {
-    // Hi-Z and environment pyramids: 32 x 32 tiles through level 5, levels 6.. by the block
-    // that finishes a pyramid's last tile
+    // Hi-Z and environment pyramids: 16 x 16 tiles through level 4, levels 5.. by the block
+    // that finishes a pyramid's last item
     const EnvInfo& e = A.e;
     if (item < F.n_hz) {
       const int v = item / (F.hx * F.hy), r = item - v * F.hx * F.hy;
-      hiz_tile_block(A.depth, A.vs.H, A.vs.W, A.hz, F.hiz, v, r % F.hx, r / F.hx, s_tile);
-      if (A.levels > 6 && last_arrival(F.ctl + kHizDone + v, F.hx * F.hy)) hiz_upper_block(A.hz, v, F.hiz);
+      for (int sub = 0; sub < 4; ++sub) {
+        const int tx = 2 * (r % F.hx) + (sub & 1), ty = 2 * (r / F.hx) + (sub >> 1);
+        if (tx * kFusedTile < A.vs.W && ty * kFusedTile < A.vs.H)  // block-uniform
+          hiz_tile_block<kFusedTile>(A.depth, A.vs.H, A.vs.W, A.hz, F.hiz, v, tx, ty, s_u.tile);
+      }
+      if (A.levels > kFusedTileLevels + 1 && last_arrival(F.ctl + kHizDone + v, F.hx * F.hy))
+        hiz_upper_block(A.hz, v, F.hiz, kFusedTileLevels + 1);
     } else {
       const int r = item - F.n_hz;
-      env_tile_block(F.env, e, F.mips, r % F.ex, r / F.ex, s_tile);
-      if (e.levels > 6 && last_arrival(F.ctl + kEnvDone, F.ex * F.ey)) env_upper_block(e, F.mips);
+      env_tile_block<kFusedTile>(F.env, e, F.mips, r % F.ex, r / F.ex, s_u.tile);
+      if (e.levels > kFusedTileLevels + 1 && last_arrival(F.ctl + kEnvDone, F.ex * F.ey))
+        env_upper_block(e, F.mips, kFusedTileLevels + 1);
     }
   } else if (ph == 2) {
     for (int c = item * kShadeChunks; c < (item + 1) * kShadeChunks; ++c) {
@@ -187,12 +204,12 @@ __global__ void __launch_bounds__(kFusedThreads, 7) k_step_fused(const __grid_co
     // Monte-Carlo adjoint (each thread's own pixel: its hits and dL/dfinal are this thread's)
     const int v = item / (F.tx * F.ty), r = item - v * F.tx * F.ty;
     const int x = (r % F.tx) * 16 + (threadIdx.x % 16), y = (r / F.tx) * 8 + (threadIdx.x / 16);
-    fill_levels(A, v, s_lv);
+    fill_levels(A, v, s_u.lv);
     __syncthreads();
     float acc = 0.0f;
     const float inv = 1.0f / (float)(npx * 3);
     if (x < A.vs.W && y < A.vs.H) {
-      const float3 fin = trace_pixel<kCid>(A, x, y, v, s_lv);
+      const float3 fin = trace_pixel<kCid>(A, x, y, v, s_u.lv);
       const long long p = v * HW + (long long)y * A.vs.W + x;
       float3 gfin;
       acc = (A.flags & SSGI_SRGB_LOSS) ? l2_srgb_pixel(A, p, fin, inv, gfin) : l2_pixel(A, p, fin, inv, gfin);
@@ -331,11 +348,11 @@ ssgi_status ssgi_step_fused(const ssgi_gbuffer* g, const ssgi_camera* cams, cons
 
   const long long nch = (npx + kFusedThreads - 1) / kFusedThreads;
   const int H = g->d.height, W = g->d.width, V = g->d.views;
-  F.hx = (W + kHizTile - 1) / kHizTile;
-  F.hy = (H + kHizTile - 1) / kHizTile;
+  F.hx = (W + kFusedRegion - 1) / kFusedRegion;
+  F.hy = (H + kFusedRegion - 1) / kFusedRegion;
   F.n_hz = p->hiz_levels > 1 ? F.hx * F.hy * V : 0;
-  F.ex = env_w / std::min(kHizTile, env_w);
-  F.ey = env_h / std::min(kHizTile, env_h);
+  F.ex = env_w / std::min(kFusedTile, env_w);
+  F.ey = env_h / std::min(kFusedTile, env_h);
   F.tx = (W + 15) / 16;
   F.ty = (H + 7) / 8;
   const long long clear = (F.n_gc1 + F.n_gmips + kClearPerBlock - 1) / kClearPerBlock;

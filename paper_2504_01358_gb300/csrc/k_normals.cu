@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) k_hiz_normals_tile(Views vs, const float*
     }
   }
   __syncthreads();
-  if (hz.levels > 1) hiz_tile_reduce(H, W, hz, hiz, view, blockIdx.x, blockIdx.y, s);
+  if (hz.levels > 1) hiz_tile_reduce<kHizTile>(H, W, hz, hiz, view, blockIdx.x, blockIdx.y, s);
 }
 
 __global__ void __launch_bounds__(256) k_hiz_normals_upper(HizInfo hz, float* hiz) {

@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(256) k_brdf_lut(int N, int M, float* __restric
 // shared memory, then one block builds levels 6.. from level 5.
 __global__ void __launch_bounds__(256) k_env_tiles(const float* env0, EnvInfo e, float* mips) {
   __shared__ TileBuf s;
-  env_tile_block(env0, e, mips, blockIdx.x, blockIdx.y, s);
+  env_tile_block<kHizTile>(env0, e, mips, blockIdx.x, blockIdx.y, s);
 }
 
 __global__ void __launch_bounds__(256) k_env_upper(EnvInfo e, float* mips) { env_upper_block(e, mips); }
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(256) k_env_upper(EnvInfo e, float* mips) { env
 __global__ void __launch_bounds__(256) k_hiz_tile(const float* __restrict__ depth, int H, int W, HizInfo hz,
                                                   float* __restrict__ hiz) {
   __shared__ TileBuf s;
-  hiz_tile_block(depth, H, W, hz, hiz, blockIdx.z, blockIdx.x, blockIdx.y, s);
+  hiz_tile_block<kHizTile>(depth, H, W, hz, hiz, blockIdx.z, blockIdx.x, blockIdx.y, s);
 }
 
 __global__ void __launch_bounds__(256) k_hiz_upper(HizInfo hz, float* hiz) { hiz_upper_block(hz, blockIdx.x, hiz); }

@@ -62,20 +62,30 @@ __device__ __forceinline__ void env_down_item(const float* src, int hs, int ws, 
 
 constexpr int kHizTile = 32;  // level-0 pixels per block side; covers levels 1..5
 
-typedef float TileBuf[kHizTile][kHizTile + 1];
+// A kT x kT tile in shared memory (a padded row: no bank conflicts on the 2 x 2 reads).
+template <int kT>
+using TileBufT = float[kT][kT + 1];
+typedef TileBufT<kHizTile> TileBuf;
 
-// Block-level: reduces the 32 x 32 level-0 tile in s (filled by the caller, +inf outside the
-// image; the caller synchronised after filling it) through levels 1..5 of the pyramid and
-// writes them; every thread of the block calls it for the same tile (it synchronises the
+// Pyramid levels a kT x kT tile covers (levels 1..log2 kT).
+template <int kT>
+__host__ __device__ constexpr int tile_levels() {
+  return kT == 1 ? 0 : 1 + tile_levels<kT / 2>();
+}
+
+// Block-level: reduces the kT x kT level-0 tile in s (filled by the caller, +inf outside the
+// image; the caller synchronised after filling it) through levels 1..log2 kT of the pyramid
+// and writes them; every thread of the block calls it for the same tile (it synchronises the
 // block); the block has at least 128 threads.
+template <int kT>
 __device__ __forceinline__ void hiz_tile_reduce(int H, int W, const HizInfo& hz, float* __restrict__ hiz, int view,
-                                                int tile_x, int tile_y, TileBuf& s) {
-  const int bx = tile_x * kHizTile, by = tile_y * kHizTile;
+                                                int tile_x, int tile_y, TileBufT<kT>& s) {
+  const int bx = tile_x * kT, by = tile_y * kT;
   float* out = hiz + (size_t)view * hz.per_view;
-  int n = kHizTile;
-  const int top = min(hz.levels - 1, 5);
-  // a level has at most 16 x 16 outputs: with >= 128 threads each thread owns at most two
-  constexpr int kPer = (kHizTile / 2) * (kHizTile / 2) / 128;
+  int n = kT;
+  const int top = min(hz.levels - 1, tile_levels<kT>());
+  // a level has at most (kT / 2)^2 outputs: with >= 128 threads each thread owns at most kPer
+  constexpr int kPer = ((kT / 2) * (kT / 2) + 127) / 128;
   for (int l = 1; l <= top; ++l) {
     n >>= 1;
     float m[kPer];
@@ -106,17 +116,19 @@ __device__ __forceinline__ void hiz_tile_reduce(int H, int W, const HizInfo& hz,
 }
 
 // Block-level: loads the tile of depth and reduces it (hiz_tile_reduce).
+template <int kT>
 __device__ __forceinline__ void hiz_tile_block(const float* __restrict__ depth, int H, int W, const HizInfo& hz,
-                                               float* __restrict__ hiz, int view, int tile_x, int tile_y, TileBuf& s) {
-  const int bx = tile_x * kHizTile, by = tile_y * kHizTile;
+                                               float* __restrict__ hiz, int view, int tile_x, int tile_y,
+                                               TileBufT<kT>& s) {
+  const int bx = tile_x * kT, by = tile_y * kT;
   const float* d0 = depth + (size_t)view * H * W;
-  for (int k = threadIdx.x; k < kHizTile * kHizTile; k += blockDim.x) {
-    const int ty = k / kHizTile, tx = k % kHizTile;
+  for (int k = threadIdx.x; k < kT * kT; k += blockDim.x) {
+    const int ty = k / kT, tx = k % kT;
     const int y = by + ty, x = bx + tx;
     s[ty][tx] = (y < H && x < W) ? __ldg(d0 + (size_t)y * W + x) : INFINITY;
   }
   __syncthreads();
-  hiz_tile_reduce(H, W, hz, hiz, view, tile_x, tile_y, s);
+  hiz_tile_reduce<kT>(H, W, hz, hiz, view, tile_x, tile_y, s);
 }
 
 __device__ __forceinline__ void hiz_level_item(const HizInfo& hz, int l, float* __restrict__ hiz, int t) {
@@ -134,20 +146,21 @@ __device__ __forceinline__ void hiz_level_item(const HizInfo& hz, int l, float* 
   hiz[(size_t)view * hz.per_view + hz.off[l] + rem] = m;
 }
 
-// Block-level: a 32 x 32 texel tile of the base environment level (tiles are exact: the sizes
-// are powers of two) copied into level 0 of the chain and reduced through level 5 in shared
-// memory, one channel at a time, with env_down_item's arithmetic.
+// Block-level: a kT x kT texel tile of the base environment level (tiles are exact: the sizes
+// are powers of two) copied into level 0 of the chain and reduced through level log2 kT in
+// shared memory, one channel at a time, with env_down_item's arithmetic.
+template <int kT>
 __device__ __forceinline__ void env_tile_block(const float* __restrict__ env0, const EnvInfo& e, float* mips,
-                                               int tile_x, int tile_y, TileBuf& s) {
+                                               int tile_x, int tile_y, TileBufT<kT>& s) {
   const int w0 = e.w[0];
-  const int th = min(kHizTile, e.h[0]), tw = min(kHizTile, w0);
+  const int th = min(kT, e.h[0]), tw = min(kT, w0);
   const int by = tile_y * th, bx = tile_x * tw;
   for (int k = threadIdx.x; k < th * tw * 3; k += blockDim.x) {
     const size_t o = ((size_t)(by + k / (tw * 3)) * w0 + bx) * 3 + k % (tw * 3);
     mips[e.off[0] + o] = __ldg(env0 + o);
   }
-  const int top = min(e.levels - 1, 5);
-  constexpr int kPer = (kHizTile / 2) * (kHizTile / 2) / 128;
+  const int top = min(e.levels - 1, tile_levels<kT>());
+  constexpr int kPer = ((kT / 2) * (kT / 2) + 127) / 128;
   for (int c = 0; c < 3; ++c) {
     __syncthreads();
     for (int k = threadIdx.x; k < th * tw; k += blockDim.x)
@@ -182,9 +195,9 @@ __device__ __forceinline__ void env_tile_block(const float* __restrict__ env0, c
   }
 }
 
-// Block-level: environment levels 6.. from level 5 (which is complete).
-__device__ __forceinline__ void env_upper_block(const EnvInfo& e, float* mips) {
-  for (int l = 6; l < e.levels; ++l) {
+// Block-level: environment levels `from`.. from level from - 1 (which is complete).
+__device__ __forceinline__ void env_upper_block(const EnvInfo& e, float* mips, int from = 6) {
+  for (int l = from; l < e.levels; ++l) {
     for (int t = threadIdx.x; t < e.h[l] * e.w[l] * 3; t += blockDim.x)
       env_down_item(mips + e.off[l - 1], e.h[l - 1], e.w[l - 1], mips + e.off[l], t);
     __threadfence();
@@ -192,9 +205,9 @@ __device__ __forceinline__ void env_upper_block(const EnvInfo& e, float* mips) {
   }
 }
 
-// Block-level: Hi-Z levels 6.. of one view from its level 5 (which is complete).
-__device__ __forceinline__ void hiz_upper_block(const HizInfo& hz, int view, float* hiz) {
-  for (int l = 6; l < hz.levels; ++l) {
+// Block-level: Hi-Z levels `from`.. of one view from its level from - 1 (which is complete).
+__device__ __forceinline__ void hiz_upper_block(const HizInfo& hz, int view, float* hiz, int from = 6) {
+  for (int l = from; l < hz.levels; ++l) {
     const int n = hz.w[l] * hz.h[l];
     for (int t = threadIdx.x; t < n; t += blockDim.x) hiz_level_item(hz, l, hiz, view * n + t);
     __threadfence();

@@ -107,3 +107,44 @@ def test_fused_phase_wait_gives_up_and_the_next_step_is_clean():
     got = {k: v.cpu().numpy() for k, v in out.items() if k != "_workspace"}
     got["loss"] = float(got["loss"][0])
     _compare(got, _per_stage(S, wl, lut))
+
+
+def _up256(n):
+    return (n + 255) & ~255
+
+
+@pytest.mark.parametrize("H,W,levels,he,we", [(61, 97, 8, 32, 64), (77, 133, 9, 64, 128), (33, 200, 3, 8, 16),
+                                              (150, 40, 16, 128, 256), (16, 16, 2, 2, 4)])
+def test_fused_pyramids_equal_the_stand_alone_builders(H, W, levels, he, we):
+    """The Hi-Z pyramid and the environment mip chain the fused step builds in its workspace
+    (its own tiling: 16 x 16 tiles through level 4, the levels above by the block that finishes
+    a pyramid's last item) equal ssgi_build_hiz and ssgi_build_env_mips bit for bit: minima and
+    2 x 2 means of the same four values in the same order, however the work is cut.  The
+    workspace holds a 512-byte control block, then the mip chain, then the pyramid (each start
+    256-byte aligned)."""
+    import paper_2504_01358_gb300 as S
+    scene = si.make_scene(41, 6, 4.0, 1)
+    cams = [si.look_at((5 * np.sin(a), 1.5, 5 * np.cos(a)), (0, 0.3, 0)) for a in (0.4, 2.6, 4.4)]
+    bufs = [si.raycast_gbuffer(scene, c, H, W) for c in cams]
+    st = lambda k: np.stack([b[k] for b in bufs])  # noqa: E731
+    wl = si.Workload(f"3view-{H}x{W}", st("depth"), st("normal"), st("albedo"), st("rough"), st("metal"),
+                     np.stack(cams), si.lognormal_env(43, he, we),
+                     si.TraceParams(spp=4, max_steps=24, seed=7, hiz_levels=levels), si.uniform_target(44, 3, H, W))
+    lut = S.ssgi_build_brdf_lut()
+    g, env, cams_d, tgt = S.to_device_workload(wl)
+    p = S.params_of(wl.params)
+    out = S.ssgi_step_fused(g, cams_d, env, lut, tgt, p)
+    torch.cuda.synchronize()
+    assert not S.ssgi_step_fused_check(out["_workspace"])
+    ws = out["_workspace"]
+    n_mips = S.ssgi_env_mip_floats(he, we)
+    n_hiz = S.ssgi_hiz_floats((3, H, W), levels)
+    o_mips = 512
+    o_hiz = o_mips + _up256(4 * n_mips)
+    mips_f = ws[o_mips:o_mips + 4 * n_mips].view(torch.float32).cpu().numpy()
+    mips_s = S.ssgi_build_env_mips(env).mips.cpu().numpy()
+    assert np.array_equal(mips_f.view(np.uint32), mips_s.view(np.uint32))
+    if levels > 1:
+        hiz_f = ws[o_hiz:o_hiz + 4 * n_hiz].view(torch.float32).cpu().numpy()
+        hiz_s = S.ssgi_build_hiz(g.depth, levels).cpu().numpy()[:n_hiz]
+        assert np.array_equal(hiz_f.view(np.uint32), hiz_s.view(np.uint32))
