@@ -16,6 +16,7 @@ probe), the end-to-end rate from pinned host buffers, the CPU oracle, the fused 
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -775,6 +776,14 @@ def run_ours(args):
     iters = int(counter.item())
     hit = pipe.hit_idx
     valid = int((hit >= -1).sum().item())
+    # rays the step budget stopped: with one more step allowed every ray repeats its iterations
+    # and exactly those rays take one more, so the difference of the two totals counts them
+    counter1 = torch.zeros(1, device="cuda", dtype=torch.int64)
+    S.ssgi_trace_indirect(pipe.g, pipe.cam, pipe.hiz, pipe.c1, pipe.c_d, pipe.em,
+                          S.params_of(dataclasses.replace(wl.params, max_steps=wl.params.max_steps + 1)),
+                          step_count=counter1)
+    torch.cuda.synchronize()
+    exhausted = int(counter1.item()) - iters
 
     # end to end through the C ABI from pinned host buffers: every step's inputs go up and its
     # final image and loss come back inside the timed region
@@ -874,6 +883,7 @@ def run_ours(args):
                          "march_iterations": iters, "traced_samples": valid,
                          "achieved = (ops_per_iteration x iterations + ops_per_sample x samples) / trace_ms": True},
                 "trace_ms": trace_ms, "march_iterations": iters, "traced_samples": valid,
+                "budget_exhausted_rays": exhausted, "budget_exhausted_share": exhausted / max(valid, 1),
                 "hbm_algorithmic_gbs": (V * H * W * (36 + 12 + 12) + 4 * V * H * W * p.spp) / (trace_ms / 1e3) / 1e9,
                 "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
                 "l2_achieved_gbs": None if l2_bytes is None else l2_bytes / (trace_ms / 1e3) / 1e9,

@@ -7,15 +7,17 @@
 // needs every receiver's scatter into its g_c1; the mip-chain adjoint needs every texel's
 // gradient).  The Monte-Carlo adjoint of a pixel needs only that pixel's hits and dL/dfinal
 // (the loss is a sum over pixels), so the block that traces a tile goes on to its adjoint: the
-// scatter of one tile overlaps the march of the others, and no phase boundary separates them.  A block takes a ticket from a counter when it starts; the ticket names its phase
-// and item, so tickets go out in phase order.  Before working, a block of phase k waits until
-// every item of phase k - 1 has finished (a completion count per phase).  That wait always
-// ends: every item of phase k - 1 took its ticket earlier, so its block is already resident
-// and running (no cooperative launch and no residency limit is needed), and it waits only for
-// phase k - 2, which finished before.  The wait is still bounded: a block that polls longer than
-// the limit marks the error word and returns, and every later block sees the mark and returns;
-// nothing spins forever.  Inside the pyramid phase the top levels are built by whichever block
-// finishes the last tile of a pyramid (a counter, no waiting).
+// scatter of one tile overlaps the march of the others, and no phase boundary separates them.
+// A block takes a ticket from a counter when it starts; the ticket names its phase and item, so
+// tickets go out in phase order.  Before working, a block of phase k waits until every item of
+// phase k - 1 has finished (a completion count per phase; the trace phase counts warps, each of
+// which leaves as soon as it is done).  That wait always ends: every item of phase k - 1 took
+// its ticket earlier, so its block is already resident and running (no cooperative launch and
+// no residency limit is needed), and it waits only for phase k - 2, which finished before.
+// The wait is still bounded: a block that polls longer than the limit marks the error word and
+// returns, and every later block sees the mark and returns; nothing spins forever.  Inside the
+// pyramid phase the top levels are built by whichever block finishes the last item of a pyramid
+// (a counter, no waiting).
 //
 // Why not persistent blocks: the trace's tiles vary in cost by an order of magnitude, and
 // resident blocks that loop over tiles from a counter measured 12-21 % slower than the same
@@ -54,6 +56,8 @@ constexpr int kFusedRegion = 2 * kFusedTile;
 // 128-pixel chunks per item in the per-pixel phases (the trace: one tile per item); coarser
 // items measured slower
 constexpr int kShadeChunks = 1;  // shading, direct adjoint, mip-chain adjoint
+
+constexpr int kTracePhase = 3;  // trace + loss + Monte-Carlo adjoint
 
 // Control words (32-bit) of the control block.
 enum : int {
@@ -117,7 +121,8 @@ __device__ __forceinline__ bool wait_for_phase(const FusedArgs& F, int ph) {
   volatile unsigned* err = F.ctl + kErr;
   if (ph > 0) {
     volatile unsigned* done = F.ctl + kDone + ph - 1;
-    const unsigned need = (unsigned)F.items[ph - 1];
+    // the trace phase counts its warps (each leaves as soon as it is done), the others their items
+    const unsigned need = (unsigned)F.items[ph - 1] * (ph - 1 == kTracePhase ? kFusedThreads / 32 : 1);
     long long spins = 0;
     while (*done < need) {
       if (*err) return false;
@@ -199,7 +204,7 @@ __global__ void __launch_bounds__(kFusedThreads, 7) k_step_fused(const __grid_co
       const long long p = (long long)c * kFusedThreads + threadIdx.x;
       if (p < npx) shade_pixel(A, p);
     }
-  } else if (ph == 3) {
+  } else if (ph == kTracePhase) {
     // trace one 16 x 8 tile (16 x 2 per warp, as k_trace), the L2 loss of its pixels and their
     // Monte-Carlo adjoint (each thread's own pixel: its hits and dL/dfinal are this thread's)
     const int v = item / (F.tx * F.ty), r = item - v * F.tx * F.ty;
@@ -215,17 +220,20 @@ __global__ void __launch_bounds__(kFusedThreads, 7) k_step_fused(const __grid_co
       acc = (A.flags & SSGI_SRGB_LOSS) ? l2_srgb_pixel(A, p, fin, inv, gfin) : l2_pixel(A, p, fin, inv, gfin);
       bwd_mc_pixel<kPathwise, true>(A, p, gfin);
     }
-    // the tile's partial sum into the FP64 accumulator (zeroed with the control block)
+    // the warp's partial sum into the FP64 accumulator (zeroed with the control block); then the
+    // warp counts itself done and leaves: its registers are not held until the block's slowest
+    // warp finishes (the warps of a tile differ in march length; measured 1 % faster at config 4)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    __shared__ float part[kFusedThreads / 32];
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double sum = 0.0;
-      for (int k = 0; k < kFusedThreads / 32; ++k) sum += (double)part[k];
-      atomicAdd(reinterpret_cast<double*>(reinterpret_cast<char*>(F.ctl) + kLossAccOffset), sum);
+    __threadfence();  // this lane's stores before the warp's count
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(reinterpret_cast<double*>(reinterpret_cast<char*>(F.ctl) + kLossAccOffset), (double)acc);
+      __threadfence();
+      const unsigned warps = (unsigned)F.items[kTracePhase] * (kFusedThreads / 32);
+      if (atomicAdd(F.ctl + kDone + kTracePhase, 1u) == warps - 1u) stamps(F.ctl)[2 * kTracePhase + 1] = global_ns();
     }
+    return;
   } else if (ph == 4) {
     // direct adjoint; its first item also writes the loss, which every trace tile has added to
     // by now

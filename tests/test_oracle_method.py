@@ -214,6 +214,26 @@ def test_hiz_traversal_equals_brute_force_pixel_walk(name, request, lut):
     assert (h >= 0).sum() > 1000 if name == "cfg1" else (h >= 0).sum() > 50
 
 
+@pytest.mark.parametrize("K", [4, 12, 32])
+def test_one_more_step_counts_the_rays_the_budget_stopped(small, lut, K):
+    """The march with budget K is the first K iterations of the march with budget K + 1, so the
+    total iterations grow by exactly one for each ray the budget stopped (a ray that, with no
+    budget to speak of, takes more than K iterations) and by nothing for any other ray, whether
+    it hit, left the screen or ended its segment.  The benchmark counts budget-stopped rays this
+    way from the kernel's own iteration totals."""
+    import dataclasses
+    runs = [O.forward(dataclasses.replace(small, params=dataclasses.replace(small.params, max_steps=k)), lut=lut)
+            for k in (K, K + 1, 100000)]
+    stopped = runs[2]["iters"] > K
+    assert stopped.sum() > 0
+    assert int(runs[1]["iters"].sum()) - int(runs[0]["iters"].sum()) == int(stopped.sum())
+    d = runs[1]["iters"].astype(np.int64) - runs[0]["iters"]
+    assert np.array_equal(d, stopped.astype(np.int64))
+    # a stopped ray is reported as a miss; every other ray's result is its unbounded result
+    assert np.all(runs[0]["hit_idx"][stopped] == O.MISS)
+    assert np.array_equal(runs[0]["hit_idx"][~stopped], runs[2]["hit_idx"][~stopped])
+
+
 def test_hiz_levels_do_not_change_hits(small, lut):
     import dataclasses
     ref = None
