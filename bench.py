@@ -364,14 +364,34 @@ def oracle_step(wl, lut):
     r = O.forward(wl, lut=lut)
     g_final = 2.0 * (r["final"] - wl.target) / r["final"].size
     He, We = wl.env.shape[:2]
-    O.backward(wl.depth, wl.normal, wl.albedo, wl.rough, wl.metal, wl.cams, r["mips"], He, We, lut, r["c1"],
-               r["hit_idx"], g_final, wl.params.spp, wl.params.seed, wl.params.flags)
+    r["grads"] = O.backward(wl.depth, wl.normal, wl.albedo, wl.rough, wl.metal, wl.cams, r["mips"], He, We, lut,
+                            r["c1"], r["hit_idx"], g_final, wl.params.spp, wl.params.seed, wl.params.flags)
     return r
 
 
-def cpu_baseline(wl):
+def parity_record(gpu, r):
+    """The timed GPU step's outputs against the oracle's whole step on the same inputs: hit
+    indices bit for bit, per-pixel RGB |gpu - oracle|_inf / max(|oracle|_inf, 1e-3), and each
+    gradient buffer's largest error relative to its scale.  The pixels over 1e-4 are the
+    rounding cases the parity tests replay at the GPU's own coordinates."""
+    import numpy as np
+    fin = gpu["final"].astype(np.float64)
+    err = np.abs(fin - r["final"]).max(axis=-1) / np.maximum(np.abs(r["final"]).max(axis=-1), 1e-3)
+    grads = {}
+    for k, g in gpu["grads"].items():
+        o = r["grads"][k]
+        grads[k] = float(np.abs(g.astype(np.float64) - o).max() / max(float(np.abs(o).max()), 1e-30))
+    return {"hit_index_match": float((gpu["hit_idx"] == r["hit_idx"]).mean()),
+            "pixels_within_1e-4": float((err <= 1e-4).mean()), "pixels_over_1e-4": int((err > 1e-4).sum()),
+            "max_pixel_rel_err": float(err.max()), "grad_max_err_over_scale": grads,
+            "reference": "the oracle's last whole step above (FP64) against the timed step's final image, "
+                         "hit indices and gradients"}
+
+
+def cpu_baseline(wl, gpu_out=None):
     """The oracle on the host cores: five whole steps at all cores, then the trace stage of a
-    seeded 65,536-pixel sample at one thread (the same binary, FP64)."""
+    seeded 65,536-pixel sample at one thread (the same binary, FP64); with the timed GPU step's
+    outputs, also their parity against the last of those steps."""
     import numpy as np
     import oracle as O
     lut = O.build_lut()
@@ -394,7 +414,8 @@ def cpu_baseline(wl):
         dt1 = time.perf_counter() - t1
     finally:
         O.set_threads(cores)
-    return {"value": rays / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    par = None if gpu_out is None else parity_record(gpu_out, r)
+    return {"value": rays / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "parity": par,
             "sample": f"{reps} whole steps of the same workload ({rays} rays each: FP64 direct shading, Hi-Z, "
                       f"trace, Monte-Carlo sum and adjoint, OpenMP over pixels), {dt:.2f} s wall per step",
             "single_thread": {"value": len(pl) * p.spp / dt1, "unit": UNIT, "cores": 1,
@@ -645,6 +666,11 @@ def run_ours(args):
     value = whole_job_rate(rays, world, ms)
     trace_ms = stage_ms["trace"]
     launches = pipe.kernels_per_step() * args.steps
+    # the timed step's outputs, for the oracle's parity record (rank 0 at one GPU only)
+    gpu_out = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        gpu_out = {"final": pipe.final.cpu().numpy(), "hit_idx": pipe.hit_idx.cpu().numpy(),
+                   "grads": {k: v.cpu().numpy() for k, v in pipe.grads.items()}}
 
     # the pathwise adjoint (SSGI_PATHWISE) of the same frame next to the replay one (untimed in the step)
     from paper_2504_01358_gb300._native import PATHWISE as N_PATHWISE
@@ -904,7 +930,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl)
+        cpu = cpu_baseline(wl, gpu_out)
     serving = serving_sustained = None
     if rank == 0 and not args.no_serving:
         pipe = None

@@ -50,3 +50,23 @@ def test_whole_job_rate_and_alu_peak_arithmetic():
         (29 * 320e6 + 100 * 12.7e6) / 2.5e-3 / 1e9)
     # one rank, 23.04 M rays in 3.2 ms
     assert bench.whole_job_rate(23040000.0, 1, 3.2) == pytest.approx(7.2e9)
+
+
+def test_parity_record_counts_pixels_hits_and_gradient_errors():
+    """The bench's parity record: per-pixel RGB error relative to max(|oracle|_inf, 1e-3), hit
+    agreement per sample, gradient error relative to each buffer's scale."""
+    import numpy as np
+    orc = {"final": np.ones((1, 2, 2, 3)), "hit_idx": np.array([[[[1, 2], [3, 4]], [[5, 6], [7, 8]]]], np.int32),
+           "grads": {"rough": np.array([[[1.0, -2.0], [0.5, 0.0]]])}}
+    fin = np.ones((1, 2, 2, 3), np.float32)
+    fin[0, 0, 0, 1] = 1.0 + 3e-4   # one pixel over 1e-4
+    fin[0, 1, 1, 2] = 1.0 + 5e-5   # one within
+    hits = orc["hit_idx"].copy()
+    hits[0, 0, 1, 0] = -1          # one of eight samples differs
+    gpu = {"final": fin, "hit_idx": hits, "grads": {"rough": np.array([[[1.0, -2.002], [0.5, 0.0]]], np.float32)}}
+    rec = bench.parity_record(gpu, orc)
+    assert rec["pixels_over_1e-4"] == 1
+    assert rec["pixels_within_1e-4"] == 0.75
+    assert abs(rec["max_pixel_rel_err"] - 3e-4) < 1e-6
+    assert rec["hit_index_match"] == 7 / 8
+    assert abs(rec["grad_max_err_over_scale"]["rough"] - 0.001) < 1e-6
