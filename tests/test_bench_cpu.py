@@ -53,20 +53,26 @@ def test_whole_job_rate_and_alu_peak_arithmetic():
 
 
 def test_parity_record_counts_pixels_hits_and_gradient_errors():
-    """The bench's parity record: per-pixel RGB error relative to max(|oracle|_inf, 1e-3), hit
-    agreement per sample, gradient error relative to each buffer's scale."""
+    """The bench's parity record: per-pixel RGB error relative to max(|oracle|_inf, 1e-3) on the
+    pixels whose samples hit alike (and that no differing sample hits), hit agreement per
+    sample, gradient error relative to each buffer's scale on those pixels."""
     import numpy as np
-    orc = {"final": np.ones((1, 2, 2, 3)), "hit_idx": np.array([[[[1, 2], [3, 4]], [[5, 6], [7, 8]]]], np.int32),
-           "grads": {"rough": np.array([[[1.0, -2.0], [0.5, 0.0]]])}}
+    hits = np.array([[[[1, 2], [3, 4]], [[5, 6], [7, -1]]]], np.int32)  # [V=1, H=2, W=2, spp=2]
+    orc = {"final": np.ones((1, 2, 2, 3)), "hit_idx": hits,
+           "grads": {"rough": np.array([[[1.0, -2.0], [0.5, 0.25]]]), "env": np.ones((2, 4, 3))}}
     fin = np.ones((1, 2, 2, 3), np.float32)
-    fin[0, 0, 0, 1] = 1.0 + 3e-4   # one pixel over 1e-4
-    fin[0, 1, 1, 2] = 1.0 + 5e-5   # one within
-    hits = orc["hit_idx"].copy()
-    hits[0, 0, 1, 0] = -1          # one of eight samples differs
-    gpu = {"final": fin, "hit_idx": hits, "grads": {"rough": np.array([[[1.0, -2.002], [0.5, 0.0]]], np.float32)}}
+    fin[0, 0, 0, 1] = 1.0 + 3e-4   # pixel (0, 0) over 1e-4
+    fin[0, 1, 1, 2] = 1.0 + 5e-5   # pixel (1, 1) within
+    fin[0, 0, 1, 0] = 2.0          # pixel (0, 1): its sample hits differently, left out
+    hg = hits.copy()
+    hg[0, 0, 1, 0] = 0             # the GPU says pixel 0 = (0, 0), the oracle pixel 3 = (1, 1)
+    gr = np.array([[[1.0, 9.0], [0.5, 0.25]]], np.float32)
+    gr[0, 1, 0] = 0.502            # pixel (1, 0): 0.002 / scale 0.5 (the only pixel left in)
+    gpu = {"final": fin, "hit_idx": hg, "grads": {"rough": gr, "env": np.ones((2, 4, 3), np.float32)}}
     rec = bench.parity_record(gpu, orc)
-    assert rec["pixels_over_1e-4"] == 1
-    assert rec["pixels_within_1e-4"] == 0.75
-    assert abs(rec["max_pixel_rel_err"] - 3e-4) < 1e-6
     assert rec["hit_index_match"] == 7 / 8
-    assert abs(rec["grad_max_err_over_scale"]["rough"] - 0.001) < 1e-6
+    # left out: the receiver (0, 1), and the pixels either side hit: (0, 0) and (1, 1)
+    assert rec["pixels_with_a_differing_hit"] == 3 and rec["pixels_compared"] == 1
+    assert rec["pixels_over_1e-4"] == 0 and rec["pixels_within_1e-4"] == 1.0
+    assert abs(rec["grad_max_err_over_scale"]["rough"] - 0.004) < 1e-6
+    assert rec["grad_max_err_over_scale"]["env"] == 0.0
