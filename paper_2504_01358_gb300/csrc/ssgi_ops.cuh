@@ -259,9 +259,9 @@ __device__ __forceinline__ void shade_pixel(const FrameArgs& A, long long p) {
 // Output transform: tone mapping + gamma to sRGB after the composite (Sec. 3.3): clamp to
 // [0, 1], then the sRGB transfer function (IEC 61966-2-1).
 // ==========================================================================================
-// x^(1/2.4) through CUDA's fast __powf: its error grows with |y log2 x|, here at most 3.5, so the
-// encoded value stays within 2e-7 of the exact one (the transfer function's own tests bound it by
-// 4e-7); it costs the trace's epilogue less than half of what powf does.
+// x^(1/2.4) through CUDA's fast __powf: its error grows with |y log2 x|, here at most 3.5, and
+// the transfer function's tests bound the encoded value's error by 4e-7 on [0, 1]; it costs the
+// trace's epilogue less than half of what powf does.
 __device__ __forceinline__ float tonemap_srgb(float x) {
   x = fminf(fmaxf(x, 0.0f), 1.0f);
   return x <= 0.0031308f ? 12.92f * x : fmaf(1.055f, __powf(x, 1.0f / 2.4f), -0.055f);
