@@ -168,17 +168,18 @@ class ClockSampler:
 
 class BusySampler:
     """nvidia-smi's utilization.gpu (share of each sample period in which a kernel was running)
-    sampled every 100 ms while a phase runs; mean over the phase."""
+    and SM clock sampled every 100 ms while a phase runs; stop() returns the mean busy share and
+    keeps the median SM clock in `sm_mhz`."""
 
     def __init__(self, device_index: int):
-        self.idx, self.proc = device_index, None
+        self.idx, self.proc, self.sm_mhz = device_index, None, None
 
     def start(self):
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.fh = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=utilization.gpu",
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=utilization.gpu,clocks.sm",
                                           "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
@@ -193,9 +194,15 @@ class BusySampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.fh.close()
+        vals, mhz = [], []
         with open(self.path) as f:
-            vals = [float(x) for x in (ln.strip() for ln in f) if x.replace(".", "").isdigit()]
+            for ln in f:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) == 2 and all(x.replace(".", "").isdigit() for x in parts):
+                    vals.append(float(parts[0]))
+                    mhz.append(float(parts[1]))
         os.unlink(self.path)
+        self.sm_mhz = statistics.median(mhz) if mhz else None
         return statistics.mean(vals) / 100.0 if vals else None
 
 
@@ -557,6 +564,7 @@ def run_serving(n_requests: int, rate: float, slots: int, budget_gb: float):
         lat.append(t_sub - rq["arrival"] + ms / 1e3)
     served_span = max(rq["arrival"] + l for rq, l in zip(reqs, lat)) - reqs[0]["arrival"]
     served_busy = busy.stop()
+    served_mhz = busy.sm_mhz
     st = srv.stats()
     srv.close()
 
@@ -606,6 +614,7 @@ def run_serving(n_requests: int, rate: float, slots: int, budget_gb: float):
         plat.append(time.perf_counter() - t0 - rq["arrival"])
     plain_span = max(rq["arrival"] + l for rq, l in zip(reqs, plat)) - reqs[0]["arrival"]
     plain_busy = busy.stop()
+    plain_mhz = busy.sm_mhz
 
     def pct(a, q):
         import numpy as np
@@ -615,10 +624,11 @@ def run_serving(n_requests: int, rate: float, slots: int, budget_gb: float):
             "offered_rays_per_s": rays / reqs[-1]["arrival"],
             "served": {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "mean_ms": 1e3 * sum(lat) / len(lat),
                        "throughput_req_per_s": n_requests / served_span, "rays_per_s": rays / served_span,
-                       "arena_peak_gb": st["arena_bytes_peak"] / 2 ** 30, "gpu_busy_share": served_busy},
+                       "arena_peak_gb": st["arena_bytes_peak"] / 2 ** 30, "gpu_busy_share": served_busy,
+                       "sm_mhz_median": served_mhz},
             "plain": {"p50_ms": pct(plat, 50), "p99_ms": pct(plat, 99), "mean_ms": 1e3 * sum(plat) / len(plat),
                       "throughput_req_per_s": n_requests / plain_span, "rays_per_s": rays / plain_span,
-                      "gpu_busy_share": plain_busy},
+                      "gpu_busy_share": plain_busy, "sm_mhz_median": plain_mhz},
             "p99_plain_over_served": pct(plat, 99) / max(pct(lat, 99), 1e-9),
             "workload": "Poisson arrivals, resolution uniform over 640x360/1280x720/1600x900/1920x1080, spp uniform "
                         "over 4/8/16/32, scenes from the config-2 generator (pool of 4 per resolution), 128x256 "
