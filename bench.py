@@ -504,7 +504,7 @@ def serving_workload(n_requests: int, rate: float, seed: int = 5):
     return reqs
 
 
-def run_serving(n_requests: int, rate: float, slots: int, budget_gb: float):
+def run_serving(n_requests: int, rate: float, slots: int, budget_gb: float, with_resident: bool = False):
     import numpy as np
     import torch
 
@@ -533,40 +533,56 @@ def run_serving(n_requests: int, rate: float, slots: int, budget_gb: float):
     rays = sum(rq["spp"] * rq["scene"].depth.size for rq in reqs)
 
     # ---- served: continuous batching --------------------------------------------------------
-    srv = Server(int(budget_gb * (1 << 30)), max_slots=slots, queue_capacity=n_requests + 16)
-    # warm up every resolution once
-    for r in range(len(SERVE_RES)):
-        rq = next(q for q in reqs if q["res"] == r)
-        h = host[id(rq["scene"])]
-        rc, t = srv.submit(outs[r][0], envs[id(rq["env"])], params(rq), depth=h["depth"], normal=h["normal"],
-                           albedo=h["albedo"], rough=h["rough"], metal=h["metal"], cams=rq["scene"].cams)
-        srv.wait(t, 60000)
-    tickets = []
-    busy = BusySampler(torch.cuda.current_device())
-    busy.start()
-    t0 = time.perf_counter()
-    for i, rq in enumerate(reqs):
-        while time.perf_counter() - t0 < rq["arrival"]:
-            pass
-        h = host[id(rq["scene"])]
-        t_sub = time.perf_counter() - t0
-        rc, t = srv.submit(outs[rq["res"]][i % ring], envs[id(rq["env"])], params(rq), depth=h["depth"],
-                           normal=h["normal"], albedo=h["albedo"], rough=h["rough"], metal=h["metal"],
-                           cams=rq["scene"].cams)
-        if rc != N.OK:
-            raise RuntimeError(f"submit failed: {N.STATUS.get(rc, rc)}")
-        tickets.append((t, t_sub))
-    lat = []
-    for (t, t_sub), rq in zip(tickets, reqs):
-        rc, ms = srv.wait(t, 600000)
-        if rc != N.OK:
-            raise RuntimeError(f"request failed: {N.STATUS.get(rc, rc)}")
-        lat.append(t_sub - rq["arrival"] + ms / 1e3)
-    served_span = max(rq["arrival"] + l for rq, l in zip(reqs, lat)) - reqs[0]["arrival"]
-    served_busy = busy.stop()
-    served_mhz = busy.sm_mhz
-    st = srv.stats()
-    srv.close()
+    def serve_stream(resident: bool):
+        """The request stream through one server: each request ships its G-buffer (resident=False)
+        or names one of the pool's scenes registered before the stream (resident=True: G-buffer and
+        Hi-Z stay on the device).  Returns (latencies in s, span, busy share, SM MHz, stats)."""
+        srv = Server(int(budget_gb * (1 << 30)), max_slots=slots, queue_capacity=n_requests + 16)
+        sid = {}
+        if resident:
+            for rq in reqs:
+                wl = rq["scene"]
+                if id(wl) not in sid:
+                    h = host[id(wl)]
+                    sid[id(wl)] = srv.scene_add(h["depth"], h["normal"], h["albedo"], h["rough"], h["metal"], wl.cams, 8)
+
+        def submit(rq, out):
+            if resident:
+                return srv.submit(out, envs[id(rq["env"])], params(rq), scene=sid[id(rq["scene"])])
+            h = host[id(rq["scene"])]
+            return srv.submit(out, envs[id(rq["env"])], params(rq), depth=h["depth"], normal=h["normal"],
+                              albedo=h["albedo"], rough=h["rough"], metal=h["metal"], cams=rq["scene"].cams)
+
+        # warm up every resolution once
+        for r in range(len(SERVE_RES)):
+            rc, t = submit(next(q for q in reqs if q["res"] == r), outs[r][0])
+            srv.wait(t, 60000)
+        tickets = []
+        busy = BusySampler(torch.cuda.current_device())
+        busy.start()
+        t0 = time.perf_counter()
+        for i, rq in enumerate(reqs):
+            while time.perf_counter() - t0 < rq["arrival"]:
+                pass
+            t_sub = time.perf_counter() - t0
+            rc, t = submit(rq, outs[rq["res"]][i % ring])
+            if rc != N.OK:
+                raise RuntimeError(f"submit failed: {N.STATUS.get(rc, rc)}")
+            tickets.append((t, t_sub))
+        lat = []
+        for (t, t_sub), rq in zip(tickets, reqs):
+            rc, ms = srv.wait(t, 600000)
+            if rc != N.OK:
+                raise RuntimeError(f"request failed: {N.STATUS.get(rc, rc)}")
+            lat.append(t_sub - rq["arrival"] + ms / 1e3)
+        span = max(rq["arrival"] + l for rq, l in zip(reqs, lat)) - reqs[0]["arrival"]
+        share = busy.stop()
+        st = srv.stats()
+        srv.close()
+        return lat, span, share, busy.sm_mhz, st
+
+    lat, served_span, served_busy, served_mhz, st = serve_stream(False)
+    res_run = serve_stream(True) if with_resident else None
 
     # ---- plain: one request at a time, synchronous, preallocated buffers --------------------
     Hm, Wm = max(SERVE_RES)
@@ -605,6 +621,7 @@ def run_serving(n_requests: int, rate: float, slots: int, budget_gb: float):
         rq = next(q for q in reqs if q["res"] == r)
         plain_one(rq, outs[r][0])
     plat = []
+    busy = BusySampler(torch.cuda.current_device())
     busy.start()
     t0 = time.perf_counter()
     for i, rq in enumerate(reqs):
@@ -630,6 +647,13 @@ def run_serving(n_requests: int, rate: float, slots: int, budget_gb: float):
                       "throughput_req_per_s": n_requests / plain_span, "rays_per_s": rays / plain_span,
                       "gpu_busy_share": plain_busy, "sm_mhz_median": plain_mhz},
             "p99_plain_over_served": pct(plat, 99) / max(pct(lat, 99), 1e-9),
+            "served_resident": None if res_run is None else {
+                "p50_ms": pct(res_run[0], 50), "p99_ms": pct(res_run[0], 99),
+                "mean_ms": 1e3 * sum(res_run[0]) / len(res_run[0]), "throughput_req_per_s": n_requests / res_run[1],
+                "gpu_busy_share": res_run[2], "sm_mhz_median": res_run[3],
+                "p99_plain_over_served": pct(plat, 99) / max(pct(res_run[0], 99), 1e-9),
+                "scenes": "the pool's 16 scenes registered once before the stream (ssgi_serve_scene_add: "
+                          "G-buffer and Hi-Z resident); each request ships only its map and names its scene"},
             "workload": "Poisson arrivals, resolution uniform over 640x360/1280x720/1600x900/1920x1080, spp uniform "
                         "over 4/8/16/32, scenes from the config-2 generator (pool of 4 per resolution), 128x256 "
                         "log-normal env maps (pool of 32), 64 steps, 8 levels; latency = arrival to result on host"}
@@ -968,7 +992,8 @@ def run_ours(args):
         torch.cuda.empty_cache()
         serving = run_serving(args.serve_requests, args.serve_rate, args.serve_slots, 100.0)
         # a load the plain path also sustains, so that its latency is not a growing queue
-        serving_sustained = run_serving(SERVE_SUSTAINED_REQUESTS, SERVE_SUSTAINED_RATE, args.serve_slots, 100.0)
+        serving_sustained = run_serving(SERVE_SUSTAINED_REQUESTS, SERVE_SUSTAINED_RATE, args.serve_slots, 100.0,
+                                        with_resident=True)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
